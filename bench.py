@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of radiomic spatial mapping on GB300.
+
+A step maps one whole synthetic volume: discretisation, VOI packing and the
+mapping kernel (all 93 maps of every VOI voxel).  Default workload: the
+CT-like 128 x 128 x 64 volume with an ellipsoidal VOI of 200,336 voxels,
+fixed bin width 25 HU, kernel radius 2 (5^3 windows), GLCM distance 1.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl flashmap|reference]
+
+Prints one JSON line (rank 0).  `value` is voxel-features/s over the K timed
+steps measured with CUDA events on the launching stream (inputs resident in
+HBM; L2 flushed between steps); `e2e` is the same metric through
+fr_map_run_host (pinned host image in, host maps out, copies inside the timed
+region).  Under torchrun every rank maps its own replica (weak scaling, no
+collective on the data path); the timed region is bracketed by barriers and
+the slowest rank's time is reported.  `--impl reference` times the FP64 CPU
+oracle on the host cores on bounded samples of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-features/s for 3D texture maps, batched vs plain; serving p50/p99 latency"
+UNIT = "voxel-features/s"
+ALU_LANES_PER_SM = 128  # fp32/int32 lanes per Blackwell SM
+
+# DRAM bytes (read + write) per launch of fr_map_kernel from an ncu capture,
+# keyed by the SHA-256 of the CUDA sources it was taken with; a source change
+# makes the figure stale and the bench reports null.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="flashmap", choices=["flashmap", "reference"])
+    ap.add_argument("--workload", default="ct_plain",
+                    choices=["ct_plain", "tiny", "ct_large", "paper_tiled"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--tune", default="", help="brick_x,brick_y,brick_z,vpi,warps,stages")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2609_19190_gb300 import synth
+    if name == "ct_plain":
+        img, mask = synth.ct_plain(seed=2)
+        kw = dict(disc_mode=1, bin_width=25.0, kernel_radius=2, glcm_distance=1)
+        desc = ("CT-like 128x128x64 int16 (tissue means -900/-50/40/300 HU, noise sd 15), "
+                "ellipsoidal VOI, FBW 25 HU, r=2 (5^3), delta=1, 93 maps")
+    elif name == "tiny":
+        img, mask = synth.tiny(seed=1)
+        kw = dict(disc_mode=0, bin_count=16, kernel_radius=1, glcm_distance=1)
+        desc = "32^3 uniform 0..255, ball VOI r=10, FBN 16, r=1, 93 maps"
+    elif name == "ct_large":
+        img, mask = synth.ct_large(seed=3)
+        kw = dict(disc_mode=0, bin_count=64, kernel_radius=3, glcm_distance=1)
+        desc = ("CT-like 256x256x128 int16, union of 3 ellipsoids, FBN 64, r=3 (7^3), "
+                "delta=1, 93 maps")
+    else:
+        img, mask = synth.paper_tiled(reps=(2, 2, 2))
+        kw = dict(disc_mode=1, bin_width=25.0, kernel_radius=1, glcm_distance=1)
+        desc = "61x55x39 MR-like crop tiled 2x2x2 (404,904 VOI voxels), FBW 25, r=1, 93 maps"
+    return img, mask, kw, desc
+
+
+# ------------------------------------------------------------------ roofline work
+def _box_sum(csum, lo, hi):
+    """Sum over boxes [z+lo0, z+hi0] x ... of the array whose inclusive
+    cumulative sum (padded by one leading zero plane per axis) is csum;
+    returns an array over the original grid (clipped at the borders)."""
+    Z, Y, X = (d - 1 for d in csum.shape)
+    zz = np.arange(Z)[:, None, None]
+    yy = np.arange(Y)[None, :, None]
+    xx = np.arange(X)[None, None, :]
+    z0 = np.clip(zz + lo[0], 0, Z); z1 = np.clip(zz + hi[0] + 1, 0, Z)
+    y0 = np.clip(yy + lo[1], 0, Y); y1 = np.clip(yy + hi[1] + 1, 0, Y)
+    x0 = np.clip(xx + lo[2], 0, X); x1 = np.clip(xx + hi[2] + 1, 0, X)
+    S = csum
+    return (S[z1, y1, x1] - S[z0, y1, x1] - S[z1, y0, x1] - S[z1, y1, x0]
+            + S[z0, y0, x1] + S[z0, y1, x0] + S[z1, y0, x0] - S[z0, y0, x0])
+
+
+def _csum(a):
+    c = np.zeros(tuple(d + 1 for d in a.shape), dtype=np.int64)
+    c[1:, 1:, 1:] = a.astype(np.int64).cumsum(0).cumsum(1).cumsum(2)
+    return c
+
+
+def algorithmic_ops(mask, r, delta):
+    """Algorithmic work of one launch, in elementary window operations summed
+    over all VOI voxels v (N_v = |V(v)|):
+      GLCM pair visits sum_d |{u : u, u + delta d in V(v)}|,
+      GLRLM run-scan visits 13 N_v, GLSZM forward-union attempts 13 N_v,
+      GLDM / NGTDM neighbour visits 26 N_v, first-order sort N_v log2 N_v."""
+    m = (mask > 0)
+    cm = _csum(m)
+    nv = _box_sum(cm, (-r, -r, -r), (r, r, r))[m].astype(np.float64)
+    pairs = np.zeros_like(nv)
+    Z, Y, X = m.shape
+    dirs = [d for d in [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
+            if d > (0, 0, 0)]
+    for d in dirs:
+        o = tuple(delta * k for k in d)
+        # M_o(u) = mask(u) mask(u + o), for u with u + o inside the volume
+        mo = np.zeros_like(m)
+        src, dst = [], []
+        for k, n in zip(o, m.shape):
+            src.append(slice(0, max(0, n - k)) if k >= 0 else slice(-k, n))
+            dst.append(slice(k, n) if k >= 0 else slice(0, max(0, n + k)))
+        mo[tuple(src)] = m[tuple(src)] & m[tuple(dst)]
+        lo = tuple(-r + max(0, -k) for k in o)
+        hi = tuple(r - max(0, k) for k in o)
+        pairs += _box_sum(_csum(mo), lo, hi)[m]
+    sort = nv * np.log2(np.maximum(nv, 1.0))
+    return float(np.sum(pairs + 52.0 * nv + sort))
+
+
+def source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2609_19190_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of the SM clock and throttle reasons
+    while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup(n):
+    rank, world, local = 0, 1, 0
+    if "WORLD_SIZE" in os.environ and int(os.environ["WORLD_SIZE"]) > 1:
+        import torch
+        import torch.distributed as dist
+        rank = int(os.environ["RANK"])
+        world = int(os.environ["WORLD_SIZE"])
+        local = int(os.environ.get("LOCAL_RANK", rank))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_rate(img, mask, kw, seconds, seed=11):
+    """Time the oracle (as it stands) on all host cores on a seeded sample of
+    the workload's VOI voxels sized to take about `seconds`."""
+    from oracle import oracle as O
+    from paper_2609_19190_gb300 import synth
+    op = O.make_params(img.shape, disc_mode=kw["disc_mode"], bin_count=kw.get("bin_count", 16),
+                       bin_width=kw.get("bin_width", 25.0), radius=kw["kernel_radius"],
+                       distance=kw["glcm_distance"])
+    levels, ng, _, _ = O.discretise(op, img, mask)
+    cores = os.cpu_count() or 1
+    probe = synth.sample_voxels(mask, min(256 * cores, int(mask.sum())), seed)
+    t0 = time.perf_counter()
+    O.map_voxels(op, img, levels, ng, probe, nthreads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n = int(min(mask.sum(), max(probe.size, probe.size * seconds / dt)))
+    sample = synth.sample_voxels(mask, n, seed + 1)
+    t0 = time.perf_counter()
+    O.map_voxels(op, img, levels, ng, sample, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return n * 93 / dt, cores, n, dt, (op, levels, ng)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2609_19190_gb300 import synth
+    img, mask, kw, desc = workload(args.workload)
+    op = O.make_params(img.shape, disc_mode=kw["disc_mode"], bin_count=kw.get("bin_count", 16),
+                       bin_width=kw.get("bin_width", 25.0), radius=kw["kernel_radius"],
+                       distance=kw["glcm_distance"])
+    levels, ng, _, _ = O.discretise(op, img, mask)
+    cores = os.cpu_count() or 1
+    budget = 150.0 / max(1, args.steps + args.warmup)  # seconds per step
+    probe = synth.sample_voxels(mask, 128 * cores, 5)
+    t0 = time.perf_counter()
+    O.map_voxels(op, img, levels, ng, probe, nthreads=cores)
+    per_vox = (time.perf_counter() - t0) / probe.size
+    n = int(max(cores, min(mask.sum(), budget / max(per_vox, 1e-9))))
+    times = []
+    for k in range(args.warmup + args.steps):
+        sample = synth.sample_voxels(mask, n, 1000 + k)
+        t0 = time.perf_counter()
+        O.map_voxels(op, img, levels, ng, sample, nthreads=cores)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times)
+    value = args.steps * n * 93 / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "n_voi": int(mask.sum()),
+                   "sample_voxels_per_step": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d seeded VOI voxels per step (of %d), all 93 maps"
+                                   % (n, int(mask.sum()))},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_flashmap(args):
+    import torch
+    import paper_2609_19190_gb300 as fm
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    img, mask, kw, desc = workload(args.workload)
+    nz, ny, nx = img.shape
+    tune = None
+    if args.tune:
+        v = [int(t) for t in args.tune.split(",")]
+        keys = ["brick_x", "brick_y", "brick_z", "voxels_per_item", "consumer_warps", "stages",
+                "ctas_per_sm"]
+        tune = dict(zip(keys, v))
+    params = fm.fr_map_params_init(nx, ny, nz, device=local, **kw)
+    plan = fm.fr_map_plan(params, torch.from_numpy(mask), tune=tune)
+    n_voi, nf = plan.n_voi, plan.n_rows
+    img_dev = torch.from_numpy(img).to(dev)
+    out = torch.empty((nf, n_voi), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        fm.fr_map_run(plan, img_dev, out)
+    fm.fr_map_sync_status(plan)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    step_ms, kern_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fm.fr_map_run(plan, img_dev, out)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(fm.fr_plan_last_kernel_ms(plan))
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    fm.fr_map_sync_status(plan)
+    t_dev = max_over_ranks(sum(step_ms) / 1e3, world)
+    value = world * args.steps * n_voi * nf / t_dev
+
+    e2e = None
+    if not args.no_e2e:
+        img_pin = torch.from_numpy(img).pin_memory()
+        out_pin = torch.empty((nf, n_voi), dtype=torch.float32).pin_memory()
+        fm.fr_map_run_host(plan, img_pin, out_pin)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            fm.fr_map_run_host(plan, img_pin, out_pin)
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+        barrier(world)
+        e2e = {"value": world * args.steps * n_voi * nf / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(img.nbytes), "d2h_bytes_per_step": int(nf * n_voi * 4),
+               "ms_per_step": 1e3 * t_e2e / args.steps}
+
+    if rank != 0:
+        return
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    ops = algorithmic_ops(mask, kw["kernel_radius"], kw["glcm_distance"])
+    kmean = statistics.mean(kern_ms) / 1e3
+    achieved = ops / kmean / 1e9
+    peak = sms * ALU_LANES_PER_SM * sm_max * 1e6 / 1e9
+    traffic = NCU_TRAFFIC.get((args.workload, source_digest()))
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "kernel": "fr_map_kernel", "kernel_ms": 1e3 * kmean,
+            "ops_per_launch": ops,
+            "peak_basis": "%d SMs x %d int32/fp32 lanes x %.0f MHz (measured max SM clock)"
+                          % (sms, ALU_LANES_PER_SM, sm_max),
+            "hbm_gbs_achieved": (img.nbytes + 4 * nf * n_voi + 4 * n_voi) / kmean / 1e9,
+            "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, cores, n, dt, _ = oracle_rate(img, mask, kw, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d seeded VOI voxels of the workload, all 93 maps, %.1f s" % (n, dt)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "n_voi": n_voi, "maps": nf,
+                   "l2": "flushed between steps (256 MiB write, outside the events)",
+                   "replicas": "each rank maps its own copy (no data-path collective)",
+                   "launch": {"grid_note": "persistent, one producer + consumer warps per CTA",
+                              "tune": tune}},
+        "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": 4 * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_flashmap(args)
+    if "WORLD_SIZE" in os.environ and int(os.environ["WORLD_SIZE"]) > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * flashmap.h -- C ABI of the GB300 (sm_103a) radiomic spatial-mapping library
+ * (libflashmap.so).
+ *
+ * What the library computes.  Spatial mapping (paper: Introduction; "Software
+ * design and extraction modes") returns, for every voxel v of a masked volume
+ * of interest (VOI), the radiomic features of the image restricted to the
+ * local neighbourhood of v, as maps aligned with the source image.  Here:
+ *
+ *   V(v)      = { u : max(|ux-vx|, |uy-vy|, |uz-vz|) <= r } n image n VOI
+ *   map_f(v)  = feature f of the gray levels / intensities in V(v)
+ *
+ * with one discretisation of the whole VOI (fixed bin number or fixed bin
+ * width; paper: "Hybrid CUDA backend implementation", where discretisation is
+ * a preprocessing step).  The 93 features are the spatial benchmark set of
+ * Table 2: first order 18, GLCM 24, GLRLM 16, GLSZM 16, NGLDM (GLDM) 14,
+ * NGTDM 5, with the IBSI definitions the paper's backends follow.  GLCM and
+ * GLRLM features are computed per direction (13 directions, GLCM offset
+ * delta * d) and averaged over the directions whose matrix is not empty;
+ * zones are 26-connected; dependences use alpha = 0 and distance 1.
+ *
+ * Conventions shared by every entry point.
+ *   - Every call returns an fr_status; nothing aborts, throws or prints.
+ *   - Volumes are C-contiguous [nz][ny][nx] (x fastest).  Images are int16,
+ *     masks uint8 (nonzero = inside the VOI).
+ *   - The caller owns images, masks and outputs; a plan owns its device
+ *     scratch and frees it in fr_map_destroy.
+ *   - "Device pointer" means memory of the plan's CUDA device (cudaMalloc,
+ *     or a torch tensor's data_ptr()).  Streams are cudaStream_t values
+ *     passed as fr_stream_t (NULL = the legacy default stream).
+ *   - Output layout: out[row][k] float32, row-major [n_rows][n_voi].  Column
+ *     k is the k-th VOI voxel in increasing linear index (z, then y, then x);
+ *     rows are the selected features in increasing feature id.  Undefined
+ *     values (0/0, single gray level where a second is needed, ...) are NaN.
+ *   - A plan is used from one stream at a time; calls on one plan must not
+ *     overlap on the device.
+ *   - Errors that happen on the device (a level count above 255 under fixed
+ *     bin width, a bounded wait that ran out) are recorded in a plan-owned
+ *     status word; fr_map_sync_status() waits for the plan's work and
+ *     returns it.  Output contents are undefined after such an error.
+ */
+#ifndef FLASHMAP_H
+#define FLASHMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* fr_stream_t; /* = cudaStream_t */
+
+typedef enum fr_status {
+  FR_OK = 0,
+  FR_ERR_INVALID_ARG = 1,     /* a parameter is out of range or a pointer is NULL */
+  FR_ERR_EMPTY_MASK = 2,      /* the mask selects no voxel */
+  FR_ERR_TOO_MANY_LEVELS = 3, /* discretisation needs more than 255 gray levels */
+  FR_ERR_OOM = 4,             /* a device or host allocation failed */
+  FR_ERR_CUDA = 5,            /* a CUDA runtime or driver call failed */
+  FR_ERR_TIMEOUT = 6,         /* a bounded device wait ran out */
+  FR_ERR_UNSUPPORTED = 7,     /* no usable sm_103a device, or a size beyond a limit */
+  FR_ERR_MISMATCH = 8         /* arguments disagree with the plan (debug calls) */
+} fr_status;
+
+enum { FR_FBN = 0, FR_FBW = 1 };                             /* discretisation */
+enum { FR_ANCHOR_VOI_MIN = 0, FR_ANCHOR_ZERO_FLOOR = 1 };    /* FBW bin anchor  */
+enum { FR_NUM_FEATURES = 93, FR_NUM_DIRECTIONS = 13, FR_MAX_RADIUS = 7 };
+
+/* Feature id ranges (ids are stable; names from fr_feature_name). */
+enum {
+  FR_FIRSTORDER_BEGIN = 0, FR_GLCM_BEGIN = 18, FR_GLRLM_BEGIN = 42,
+  FR_GLSZM_BEGIN = 58, FR_GLDM_BEGIN = 74, FR_NGTDM_BEGIN = 88, FR_FEATURES_END = 93
+};
+
+/* Mapping parameters (the paper's settings object: feature families,
+ * discretisation, VOI handling; "Software design and extraction modes"). */
+typedef struct fr_map_params {
+  int32_t nx, ny, nz;       /* volume extents (each >= 1)                         */
+  double spacing[3];        /* voxel spacing in mm (x, y, z); TotalEnergy only    */
+  int32_t disc_mode;        /* FR_FBN or FR_FBW                                   */
+  int32_t bin_count;        /* FBN: Ng in 1..255                                  */
+  double bin_width;         /* FBW: w > 0; Ng = floor((xmax - anchor)/w) + 1      */
+  int32_t fbw_anchor;       /* FR_ANCHOR_VOI_MIN (xmin) or FR_ANCHOR_ZERO_FLOOR   */
+  int32_t kernel_radius;    /* r in 1..7: window side 2r+1                        */
+  int32_t glcm_distance;    /* delta >= 1: GLCM pairs (u, u + delta*d)            */
+  uint64_t feature_mask[2]; /* bit f (word f/64, bit f%64) selects feature id f   */
+  int32_t kurtosis_excess;  /* 1: m4/m2^2 - 3 (IBSI; default); 0: m4/m2^2         */
+  int32_t device;           /* CUDA device ordinal                                */
+  int32_t mask_on_device;   /* 1: the mask pointer is a device pointer; 0: host   */
+  int32_t reserved;         /* must be 0                                          */
+} fr_map_params;
+
+/* Launch shape of the mapping kernel (the autotuner's knobs).  Zero fields
+ * take built-in defaults. */
+typedef struct fr_tune {
+  int32_t brick_x, brick_y, brick_z; /* voxels per brick; brick_x % 4 == 0      */
+  int32_t voxels_per_item;           /* work-queue granularity (1..1024)       */
+  int32_t consumer_warps;            /* warps per CTA that map voxels (1..16)  */
+  int32_t stages;                    /* TMA halo buffers per CTA (1..4)        */
+  int32_t ctas_per_sm;               /* persistent CTAs per SM (0 = max fit)   */
+} fr_tune;
+
+typedef struct fr_plan fr_plan;
+typedef struct fr_batch fr_batch;
+
+/* Fill p with defaults for an nx * ny * nz volume: FBN 16, r = 1, delta = 1,
+ * all 93 features, unit spacing, excess kurtosis, device 0, host mask. */
+void fr_map_params_init(fr_map_params* p, int32_t nx, int32_t ny, int32_t nz);
+
+/* Plan a mapping for one mask: builds on the device the VOI voxel list (z-major),
+ * the brick schedule and the work queue, and allocates the scratch the runs
+ * need.  Synchronous.  mask: host or device pointer per p->mask_on_device.
+ * tune may be NULL.  On success *out owns everything; free it with
+ * fr_map_destroy.  Errors: INVALID_ARG, EMPTY_MASK, OOM, CUDA, UNSUPPORTED. */
+fr_status fr_map_plan(const fr_map_params* p, const uint8_t* mask,
+                      const fr_tune* tune, fr_plan** out);
+
+/* Map one image (device pointer, [nz][ny][nx] int16) into out (device pointer,
+ * float32 [n_rows][n_voi]).  Asynchronous on stream s: discretisation,
+ * packing and the mapping kernel are queued; no host synchronisation. */
+fr_status fr_map_run(fr_plan* plan, const int16_t* image, float* out,
+                     fr_stream_t s);
+
+/* Same as fr_map_run with HOST image and output buffers: copies the image to
+ * the device, maps it and copies the maps back, then waits for the stream.
+ * Pinned host memory makes the copies asynchronous DMA.  Device staging
+ * buffers are allocated by the plan on first use.  Returns the device status
+ * of the run (as fr_map_sync_status would). */
+fr_status fr_map_run_host(fr_plan* plan, const int16_t* image_host,
+                          float* out_host, fr_stream_t s);
+
+/* Wait for the plan's queued work and return the device-side status of the
+ * last run (FR_OK, FR_ERR_TOO_MANY_LEVELS or FR_ERR_TIMEOUT) or FR_ERR_CUDA. */
+fr_status fr_map_sync_status(fr_plan* plan);
+
+/* Sizes of a plan: VOI voxel count (= output columns), output rows, and the
+ * device bytes the plan holds.  Any pointer may be NULL. */
+fr_status fr_plan_query(const fr_plan* plan, int64_t* n_voi, int32_t* n_rows,
+                        size_t* device_bytes);
+
+/* Linear voxel index (z*ny + y)*nx + x of every output column, into idx
+ * (device pointer, int32 [n_voi]).  Asynchronous on s. */
+fr_status fr_plan_voxel_index(const fr_plan* plan, int32_t* idx, fr_stream_t s);
+
+/* After a run: the discretised gray levels (device pointer, uint8
+ * [nz][ny][nx], 0 outside the VOI), and into host ints the level count Ng and
+ * the VOI intensity range.  Synchronous.  Any pointer may be NULL. */
+fr_status fr_plan_levels(fr_plan* plan, uint8_t* levels, int32_t* ng,
+                         int32_t* xmin, int32_t* xmax);
+
+/* Scatter maps to dense volumes: dense[row][z][y][x] = out[row][k] at VOI
+ * voxels, NaN elsewhere (the paper's maps aligned with the source image).
+ * Device pointers; asynchronous on s. */
+fr_status fr_scatter_dense(const fr_plan* plan, const float* out, float* dense,
+                           fr_stream_t s);
+
+/* Debug: the integer texture matrices the mapping kernel builds, for n
+ * output columns cols[] (host int32) of an image (device pointer).  ng must
+ * equal the level count of this image's discretisation (else MISMATCH).  One
+ * record of fr_debug_record_ints(plan, ng) int32 per column is written to
+ * rec (device pointer), in this order:
+ *   [0..3]   ng, s = 2r+1, w = s^3, N_v
+ *   hist     [ng]            voxels of each level in V(v)
+ *   glcm     [13][ng][ng]    symmetric co-occurrence counts per direction
+ *   glrlm    [13][ng][s]     runs of level i and length j+1 per direction
+ *   glszm    [ng][w]         zones of level i and size j+1
+ *   gldm     [ng][27]        voxels of level i with j equal 26-neighbours
+ *   ngtdm_n  [ng]            voxels of level i with at least one neighbour
+ *   ngtdm_sl [ng] int64      s_i * lcm(1..26), exact (8-byte aligned)
+ * Direction d is the d-th vector (dz, dy, dx) of {-1,0,1}^3 that is
+ * lexicographically greater than (0, 0, 0).  Synchronous. */
+int64_t fr_debug_record_ints(const fr_plan* plan, int32_t ng);
+fr_status fr_debug_matrices(fr_plan* plan, const int16_t* image,
+                            const int32_t* cols, int32_t n, int32_t ng,
+                            int32_t* rec, fr_stream_t s);
+
+/* Device time in milliseconds of the mapping kernel of the plan's last run,
+ * measured by CUDA events the library records on the launching stream
+ * immediately before and after that kernel (the discretisation and packing
+ * kernels before it are excluded).  Waits for the run.  Errors: INVALID_ARG
+ * before any run. */
+fr_status fr_plan_last_kernel_ms(fr_plan* plan, float* ms);
+
+/* Free a plan (NULL is a no-op).  Waits for the plan's device work. */
+void fr_map_destroy(fr_plan* plan);
+
+/* Batched mapping (continuous-batching building block): n independent
+ * (params, mask) pairs share one persistent kernel launch fed by one device
+ * work queue of ragged items, launched as a captured CUDA graph.  params[i]
+ * and masks[i] as for fr_map_plan (all on one device).  tune may be NULL. */
+fr_status fr_batch_plan(const fr_map_params* params, const uint8_t* const* masks,
+                        int32_t n, const fr_tune* tune, fr_batch** out);
+fr_status fr_batch_query(const fr_batch* b, int32_t i, int64_t* n_voi,
+                         int32_t* n_rows);
+/* images[i] / outs[i]: device pointers, as for fr_map_run.  The pointer
+ * arrays themselves are host arrays.  Asynchronous on s. */
+fr_status fr_batch_run(fr_batch* b, const int16_t* const* images,
+                       float* const* outs, fr_stream_t s);
+fr_status fr_batch_sync_status(fr_batch* b);
+/* As fr_plan_last_kernel_ms, for the batch's persistent kernel. */
+fr_status fr_batch_last_kernel_ms(fr_batch* b, float* ms);
+void fr_batch_destroy(fr_batch* b);
+
+/* Names and helpers. */
+int32_t fr_feature_count(void);
+const char* fr_feature_name(int32_t id); /* NULL outside 0..92 */
+const char* fr_status_string(fr_status s);
+/* Direction i (0..12) as (dz, dy, dx); INVALID_ARG outside 0..12. */
+fr_status fr_direction(int32_t i, int32_t* dz, int32_t* dy, int32_t* dx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLASHMAP_H */

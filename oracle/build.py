@@ -20,7 +20,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
         return LIB_PATH
     tmp = LIB_PATH + ".tmp.%d" % os.getpid()
-    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
            "-o", tmp] + SOURCES
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB_PATH)

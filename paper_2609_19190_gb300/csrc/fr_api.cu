@@ -1,0 +1,954 @@
+// fr_api.cu -- host side of the C ABI (include/flashmap.h): parameter
+// checks, plans (VOI list, brick schedule, work items, tensor maps, scratch),
+// runs, batches with CUDA-graph launch, and the debug / export calls.
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include "../../include/flashmap.h"
+#include "fr_internal.h"
+
+namespace fr {
+// fr_map_kernel.cu
+int fr_map_smem_bytes(int stages, int tile_bytes, int nw, int arena_bytes);
+cudaError_t fr_map_configure(bool dump, int smem_bytes);
+cudaError_t fr_map_occupancy(bool dump, int threads, int smem_bytes, int* blocks);
+cudaError_t fr_map_launch(bool dump, const FrMapArgs& args, int grid, int smem_bytes,
+                          cudaStream_t s);
+// fr_prep.cu
+cudaError_t fr_launch_prepare(const FrJob* jobs, int njobs, int64_t max_voi,
+                              void* const* run_ptrs, uint32_t* queue, int32_t* status,
+                              int sms, cudaStream_t s);
+cudaError_t fr_launch_row_count(const uint8_t* mask, int nx, int rows, int32_t* rowcnt,
+                                cudaStream_t s);
+cudaError_t fr_launch_scan(const int32_t* in, int32_t* out, int n, long long* tot,
+                           cudaStream_t s);
+cudaError_t fr_launch_voi_fill(const uint8_t* mask, int nx, int rows, const int32_t* rowoff,
+                               int32_t* voi, cudaStream_t s);
+cudaError_t fr_launch_bricks(const int32_t* voi, int64_t n, int nx, int ny, int bx, int by,
+                             int bz, int nbx, int nby, int32_t* bcount, cudaStream_t s);
+cudaError_t fr_launch_brick_fill(const int32_t* voi, int64_t n, int nx, int ny, int bx, int by,
+                                 int bz, int nbx, int nby, const int32_t* boff,
+                                 int32_t* bfill, int32_t* bcols, cudaStream_t s);
+cudaError_t fr_launch_scatter(const int32_t* voi, int64_t n, int nf, int64_t nvox,
+                              const float* out, float* dense, cudaStream_t s);
+cudaError_t fr_launch_levels(const uint32_t* packed, int nx, int rows, int px,
+                             uint8_t* levels, cudaStream_t s);
+}  // namespace fr
+
+using namespace fr;
+
+namespace {
+
+// Feature names: PyRadiomics-style class_Feature names of the 93 spatial
+// benchmark maps (Table 2), in feature-id order.
+const char* const kFeatureNames[kNumFeatures] = {
+    "firstorder_Energy", "firstorder_TotalEnergy", "firstorder_Entropy",
+    "firstorder_Minimum", "firstorder_10Percentile", "firstorder_90Percentile",
+    "firstorder_Maximum", "firstorder_Mean", "firstorder_Median",
+    "firstorder_InterquartileRange", "firstorder_Range",
+    "firstorder_MeanAbsoluteDeviation", "firstorder_RobustMeanAbsoluteDeviation",
+    "firstorder_RootMeanSquared", "firstorder_Skewness", "firstorder_Kurtosis",
+    "firstorder_Variance", "firstorder_Uniformity",
+    "glcm_Autocorrelation", "glcm_JointAverage", "glcm_ClusterProminence",
+    "glcm_ClusterShade", "glcm_ClusterTendency", "glcm_Contrast",
+    "glcm_Correlation", "glcm_DifferenceAverage", "glcm_DifferenceEntropy",
+    "glcm_DifferenceVariance", "glcm_JointEnergy", "glcm_JointEntropy",
+    "glcm_Imc1", "glcm_Imc2", "glcm_Idm", "glcm_Idmn", "glcm_Id", "glcm_Idn",
+    "glcm_InverseVariance", "glcm_MaximumProbability", "glcm_SumAverage",
+    "glcm_SumEntropy", "glcm_SumSquares", "glcm_MCC",
+    "glrlm_ShortRunEmphasis", "glrlm_LongRunEmphasis",
+    "glrlm_GrayLevelNonUniformity", "glrlm_GrayLevelNonUniformityNormalized",
+    "glrlm_RunLengthNonUniformity", "glrlm_RunLengthNonUniformityNormalized",
+    "glrlm_RunPercentage", "glrlm_GrayLevelVariance", "glrlm_RunVariance",
+    "glrlm_RunEntropy", "glrlm_LowGrayLevelRunEmphasis",
+    "glrlm_HighGrayLevelRunEmphasis", "glrlm_ShortRunLowGrayLevelEmphasis",
+    "glrlm_ShortRunHighGrayLevelEmphasis", "glrlm_LongRunLowGrayLevelEmphasis",
+    "glrlm_LongRunHighGrayLevelEmphasis",
+    "glszm_SmallAreaEmphasis", "glszm_LargeAreaEmphasis",
+    "glszm_GrayLevelNonUniformity", "glszm_GrayLevelNonUniformityNormalized",
+    "glszm_SizeZoneNonUniformity", "glszm_SizeZoneNonUniformityNormalized",
+    "glszm_ZonePercentage", "glszm_GrayLevelVariance", "glszm_ZoneVariance",
+    "glszm_ZoneEntropy", "glszm_LowGrayLevelZoneEmphasis",
+    "glszm_HighGrayLevelZoneEmphasis", "glszm_SmallAreaLowGrayLevelEmphasis",
+    "glszm_SmallAreaHighGrayLevelEmphasis", "glszm_LargeAreaLowGrayLevelEmphasis",
+    "glszm_LargeAreaHighGrayLevelEmphasis",
+    "gldm_SmallDependenceEmphasis", "gldm_LargeDependenceEmphasis",
+    "gldm_GrayLevelNonUniformity", "gldm_DependenceNonUniformity",
+    "gldm_DependenceNonUniformityNormalized", "gldm_GrayLevelVariance",
+    "gldm_DependenceVariance", "gldm_DependenceEntropy",
+    "gldm_LowGrayLevelEmphasis", "gldm_HighGrayLevelEmphasis",
+    "gldm_SmallDependenceLowGrayLevelEmphasis",
+    "gldm_SmallDependenceHighGrayLevelEmphasis",
+    "gldm_LargeDependenceLowGrayLevelEmphasis",
+    "gldm_LargeDependenceHighGrayLevelEmphasis",
+    "ngtdm_Coarseness", "ngtdm_Contrast", "ngtdm_Busyness", "ngtdm_Complexity",
+    "ngtdm_Strength"};
+
+// Directions (dz, dy, dx) in the documented order.
+const int kDirs[kNumDirs][3] = {{0, 0, 1},  {0, 1, -1}, {0, 1, 0},  {0, 1, 1},
+                                {1, -1, -1}, {1, -1, 0}, {1, -1, 1}, {1, 0, -1},
+                                {1, 0, 0},  {1, 0, 1},  {1, 1, -1}, {1, 1, 0},
+                                {1, 1, 1}};
+
+constexpr long long kTimeoutNs = 10LL * 1000 * 1000 * 1000;  // 10 s per device wait
+
+struct CudaFail {
+  fr_status st;
+};
+
+#define FR_TRY(expr)                                                     \
+  do {                                                                   \
+    cudaError_t e__ = (expr);                                            \
+    if (e__ != cudaSuccess) {                                            \
+      throw CudaFail{e__ == cudaErrorMemoryAllocation ? FR_ERR_OOM        \
+                                                      : FR_ERR_CUDA};    \
+    }                                                                    \
+  } while (0)
+
+template <class T>
+T* dev_alloc(size_t count, size_t* acct) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) throw CudaFail{FR_ERR_OOM};
+  if (acct) *acct += count * sizeof(T);
+  return (T*)p;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool valid_params(const fr_map_params* p) {
+  if (!p) return false;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return false;
+  if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return false;
+  if (p->kernel_radius < 1 || p->kernel_radius > kMaxRadius) return false;
+  if (p->glcm_distance < 1 || p->glcm_distance > 2 * kMaxRadius) return false;
+  if (p->disc_mode == FR_FBN) {
+    if (p->bin_count < 1 || p->bin_count > 255) return false;
+  } else if (p->disc_mode == FR_FBW) {
+    if (!(p->bin_width > 0.0)) return false;
+    if (p->fbw_anchor != FR_ANCHOR_VOI_MIN && p->fbw_anchor != FR_ANCHOR_ZERO_FLOOR)
+      return false;
+  } else {
+    return false;
+  }
+  if (!(p->spacing[0] > 0 && p->spacing[1] > 0 && p->spacing[2] > 0)) return false;
+  if (p->reserved != 0) return false;
+  bool any = false;
+  for (int f = 0; f < kNumFeatures; ++f)
+    if ((p->feature_mask[f >> 6] >> (f & 63)) & 1ull) any = true;
+  if (!any) return false;
+  if ((p->feature_mask[1] >> (kNumFeatures - 64)) != 0ull) return false;
+  return true;
+}
+
+fr_tune default_tune(const fr_tune* t) {
+  fr_tune d;
+  d.brick_x = 16;
+  d.brick_y = 8;
+  d.brick_z = 8;
+  d.voxels_per_item = 64;
+  d.consumer_warps = 16;
+  d.stages = 2;
+  d.ctas_per_sm = 0;
+  if (t) {
+    if (t->brick_x) d.brick_x = t->brick_x;
+    if (t->brick_y) d.brick_y = t->brick_y;
+    if (t->brick_z) d.brick_z = t->brick_z;
+    if (t->voxels_per_item) d.voxels_per_item = t->voxels_per_item;
+    if (t->consumer_warps) d.consumer_warps = t->consumer_warps;
+    if (t->stages) d.stages = t->stages;
+    if (t->ctas_per_sm) d.ctas_per_sm = t->ctas_per_sm;
+  }
+  return d;
+}
+
+bool valid_tune(const fr_tune& t) {
+  return t.brick_x >= 4 && t.brick_x % 4 == 0 && t.brick_x <= 64 && t.brick_y >= 1 &&
+         t.brick_y <= 64 && t.brick_z >= 1 && t.brick_z <= 64 && t.voxels_per_item >= 1 &&
+         t.voxels_per_item <= 1024 && t.consumer_warps >= 1 &&
+         t.consumer_warps <= kMaxConsumerWarps && t.stages >= 1 && t.stages <= kMaxStages &&
+         t.ctas_per_sm >= 0;
+}
+
+// Device resources of one VOI.
+struct JobRes {
+  fr_map_params p;
+  int64_t n_voi = 0;
+  int32_t nf = 0;
+  int16_t row_of[96];
+  uint32_t families = 0;
+  int32_t px = 0;
+  int32_t ngc = 0;  // level cap of this job
+  uint32_t* packed = nullptr;
+  int32_t* voi = nullptr;
+  int32_t* bcols = nullptr;
+  FrJobState* state = nullptr;
+  std::vector<FrItem> items;  // job field = 0
+  size_t bytes = 0;
+
+  void release() {
+    cudaFree(packed);
+    cudaFree(voi);
+    cudaFree(bcols);
+    cudaFree(state);
+    packed = nullptr;
+    voi = bcols = nullptr;
+    state = nullptr;
+  }
+};
+
+void select_features(JobRes& j) {
+  int row = 0;
+  j.families = kFamFO;
+  for (int f = 0; f < kNumFeatures; ++f) {
+    bool on = (j.p.feature_mask[f >> 6] >> (f & 63)) & 1ull;
+    j.row_of[f] = on ? (int16_t)row++ : (int16_t)-1;
+    if (!on) continue;
+    if (f >= FR_GLCM_BEGIN && f < FR_GLRLM_BEGIN) j.families |= kFamGLCM;
+    if (f == FR_GLRLM_BEGIN - 1) j.families |= kFamMCC;
+    if (f >= FR_GLRLM_BEGIN && f < FR_GLSZM_BEGIN) j.families |= kFamGLRLM;
+    if (f >= FR_GLSZM_BEGIN && f < FR_GLDM_BEGIN) j.families |= kFamGLSZM;
+    if (f >= FR_GLDM_BEGIN && f < FR_NGTDM_BEGIN) j.families |= kFamGLDM;
+    if (f >= FR_NGTDM_BEGIN) j.families |= kFamNGTDM;
+  }
+  for (int f = kNumFeatures; f < 96; ++f) j.row_of[f] = -1;
+  j.nf = row;
+  j.ngc = j.p.disc_mode == FR_FBN ? j.p.bin_count : 255;
+}
+
+// Build the VOI list, brick schedule and items of one mask (synchronous).
+fr_status build_job(const fr_map_params* p, const uint8_t* mask, const fr_tune& tune,
+                    JobRes& j, cudaStream_t s) {
+  j.p = *p;
+  select_features(j);
+  const int nx = p->nx, ny = p->ny, nz = p->nz;
+  const int rows = ny * nz;
+  const int64_t nvox = (int64_t)nx * ny * nz;
+  uint8_t* dmask = nullptr;
+  int32_t *rowcnt = nullptr, *rowoff = nullptr, *bcount = nullptr, *boff = nullptr,
+          *bfill = nullptr;
+  long long* tot = nullptr;
+  fr_status st = FR_OK;
+  try {
+    const uint8_t* m = mask;
+    if (!p->mask_on_device) {
+      dmask = dev_alloc<uint8_t>(nvox, nullptr);
+      FR_TRY(cudaMemcpyAsync(dmask, mask, nvox, cudaMemcpyHostToDevice, s));
+      m = dmask;
+    }
+    rowcnt = dev_alloc<int32_t>(rows, nullptr);
+    rowoff = dev_alloc<int32_t>(rows, nullptr);
+    tot = dev_alloc<long long>(1, nullptr);
+    FR_TRY(fr_launch_row_count(m, nx, rows, rowcnt, s));
+    FR_TRY(fr_launch_scan(rowcnt, rowoff, rows, tot, s));
+    long long n = 0;
+    FR_TRY(cudaMemcpyAsync(&n, tot, sizeof(n), cudaMemcpyDeviceToHost, s));
+    FR_TRY(cudaStreamSynchronize(s));
+    if (n == 0) throw CudaFail{FR_ERR_EMPTY_MASK};
+    j.n_voi = n;
+    j.voi = dev_alloc<int32_t>(n, &j.bytes);
+    FR_TRY(fr_launch_voi_fill(m, nx, rows, rowoff, j.voi, s));
+    const int bx = tune.brick_x, by = tune.brick_y, bz = tune.brick_z;
+    const int nbx = (nx + bx - 1) / bx, nby = (ny + by - 1) / by, nbz = (nz + bz - 1) / bz;
+    const int nb = nbx * nby * nbz;
+    bcount = dev_alloc<int32_t>(nb, nullptr);
+    boff = dev_alloc<int32_t>(nb, nullptr);
+    bfill = dev_alloc<int32_t>(nb, nullptr);
+    FR_TRY(cudaMemsetAsync(bcount, 0, nb * sizeof(int32_t), s));
+    FR_TRY(cudaMemsetAsync(bfill, 0, nb * sizeof(int32_t), s));
+    FR_TRY(fr_launch_bricks(j.voi, n, nx, ny, bx, by, bz, nbx, nby, bcount, s));
+    FR_TRY(fr_launch_scan(bcount, boff, nb, tot, s));
+    j.bcols = dev_alloc<int32_t>(n, &j.bytes);
+    FR_TRY(fr_launch_brick_fill(j.voi, n, nx, ny, bx, by, bz, nbx, nby, boff, bfill, j.bcols,
+                                s));
+    std::vector<int32_t> hc(nb), ho(nb);
+    FR_TRY(cudaMemcpyAsync(hc.data(), bcount, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FR_TRY(cudaMemcpyAsync(ho.data(), boff, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FR_TRY(cudaStreamSynchronize(s));
+    const int iv = tune.voxels_per_item;
+    for (int b = 0; b < nb; ++b) {
+      if (!hc[b]) continue;
+      const int ix = b % nbx, iy = (b / nbx) % nby, iz = b / (nbx * nby);
+      for (int t = 0; t < hc[b]; t += iv) {
+        FrItem it;
+        it.job = 0;
+        it.bx = ix * bx;
+        it.by = iy * by;
+        it.bz = iz * bz;
+        it.j0 = ho[b] + t;
+        it.n = std::min(iv, hc[b] - t);
+        j.items.push_back(it);
+      }
+    }
+    j.px = (nx + 3) / 4 * 4;
+    const size_t packed_n = (size_t)j.px * ny * nz;
+    j.packed = dev_alloc<uint32_t>(packed_n, &j.bytes);
+    FR_TRY(cudaMemsetAsync(j.packed, 0, packed_n * sizeof(uint32_t), s));
+    j.state = dev_alloc<FrJobState>(1, &j.bytes);
+    FR_TRY(cudaMemsetAsync(j.state, 0, sizeof(FrJobState), s));
+    FR_TRY(cudaStreamSynchronize(s));
+  } catch (CudaFail& f) {
+    st = f.st;
+    cudaStreamSynchronize(s);
+    j.release();
+  }
+  cudaFree(dmask);
+  cudaFree(rowcnt);
+  cudaFree(rowoff);
+  cudaFree(bcount);
+  cudaFree(boff);
+  cudaFree(bfill);
+  cudaFree(tot);
+  return st;
+}
+
+// A set of jobs sharing one persistent launch.
+struct Engine {
+  int device = 0, sms = 0;
+  std::vector<JobRes> jobs;
+  std::vector<FrJob> hjobs;
+  FrJob* jobs_dev = nullptr;
+  void** run_ptrs_dev = nullptr;
+  FrItem* items_dev = nullptr;
+  int n_items = 0;
+  uint32_t* queue = nullptr;
+  int32_t* status = nullptr;
+  char* slab = nullptr;
+  int64_t slab_stride = 0;
+  int slab_ngc = 0;
+  FrArena arena{};
+  fr_tune tune{};
+  int nw = 0, stages = 0, tile_bytes = 0, smem = 0, grid = 0;
+  int64_t max_voi = 0;
+  size_t bytes = 0;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t private_stream = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaEvent_t k_begin = nullptr, k_end = nullptr;  // around the mapping kernel
+  bool ran = false;
+
+  void release() {
+    if (done) cudaEventSynchronize(done);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (private_stream) cudaStreamDestroy(private_stream);
+    if (done) cudaEventDestroy(done);
+    if (k_begin) cudaEventDestroy(k_begin);
+    if (k_end) cudaEventDestroy(k_end);
+    k_begin = k_end = nullptr;
+    for (auto& j : jobs) j.release();
+    cudaFree(jobs_dev);
+    cudaFree(run_ptrs_dev);
+    cudaFree(items_dev);
+    cudaFree(queue);
+    cudaFree(status);
+    cudaFree(slab);
+    gexec = nullptr;
+    private_stream = nullptr;
+    done = nullptr;
+    jobs_dev = nullptr;
+    run_ptrs_dev = nullptr;
+    items_dev = nullptr;
+    queue = nullptr;
+    status = nullptr;
+    slab = nullptr;
+  }
+
+  FrMapArgs args(bool dump) const {
+    FrMapArgs a{};
+    a.jobs = jobs_dev;
+    a.run_ptrs = run_ptrs_dev;
+    a.items = items_dev;
+    a.n_items = n_items;
+    a.consumer_warps = nw;
+    a.stages = stages;
+    a.tile_bytes = tile_bytes;
+    a.queue = queue;
+    a.status = status;
+    a.slab = slab;
+    a.slab_stride = slab_stride;
+    a.slab_ngc = slab_ngc;
+    a.arena = arena;
+    a.dbg = nullptr;
+    a.dbg_stride = 0;
+    a.timeout_ns = kTimeoutNs;
+    (void)dump;
+    return a;
+  }
+
+  // Everything after the jobs are built: launch shape, scratch, tensor maps.
+  fr_status finalize(cudaStream_t s) {
+    try {
+      int r_max = 1;
+      for (auto& j : jobs) {
+        r_max = std::max(r_max, j.p.kernel_radius);
+        max_voi = std::max(max_voi, j.n_voi);
+      }
+      arena = fr_make_arena(r_max);
+      tile_bytes = 0;
+      for (auto& j : jobs) {
+        const int r = j.p.kernel_radius, hx = (r + 3) / 4 * 4;
+        const int b = (tune.brick_x + 2 * hx) * (tune.brick_y + 2 * r) * (tune.brick_z + 2 * r) * 4;
+        tile_bytes = std::max(tile_bytes, b);
+      }
+      tile_bytes = fr_align(tile_bytes, 128);
+      stages = tune.stages;
+      nw = tune.consumer_warps;
+      int max_smem = 0;
+      FR_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+      while (nw > 1 && fr_map_smem_bytes(stages, tile_bytes, nw, arena.bytes) > max_smem) --nw;
+      smem = fr_map_smem_bytes(stages, tile_bytes, nw, arena.bytes);
+      if (smem > max_smem) throw CudaFail{FR_ERR_UNSUPPORTED};
+      FR_TRY(fr_map_configure(false, smem));
+      FR_TRY(fr_map_configure(true, smem));
+      int blocks = 0;
+      FR_TRY(fr_map_occupancy(false, 32 * (nw + 1), smem, &blocks));
+      if (blocks < 1) throw CudaFail{FR_ERR_UNSUPPORTED};
+      if (tune.ctas_per_sm > 0) blocks = std::min(blocks, tune.ctas_per_sm);
+      grid = sms * blocks;
+      slab_ngc = 0;
+      for (auto& j : jobs) slab_ngc = std::max(slab_ngc, j.ngc);
+      if (slab_ngc > kMCap) {
+        slab_stride = fr_align(fr_big_layout(slab_ngc, slab_ngc, arena.w_max).bytes, 256);
+        slab = dev_alloc<char>((size_t)grid * nw * slab_stride, &bytes);
+        FR_TRY(cudaMemsetAsync(slab, 0, (size_t)grid * nw * slab_stride, s));
+      } else {
+        slab_stride = 0;
+      }
+      // device job table with tensor maps
+      PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+      if (!enc) throw CudaFail{FR_ERR_CUDA};
+      hjobs.resize(jobs.size());
+      for (size_t i = 0; i < jobs.size(); ++i) {
+        JobRes& j = jobs[i];
+        FrJob& h = hjobs[i];
+        memset((void*)&h, 0, sizeof(FrJob));
+        h.packed = j.packed;
+        h.voi = j.voi;
+        h.bcols = j.bcols;
+        h.state = j.state;
+        h.n_voi = j.n_voi;
+        h.nx = j.p.nx;
+        h.ny = j.p.ny;
+        h.nz = j.p.nz;
+        h.px = j.px;
+        h.r = j.p.kernel_radius;
+        h.delta = j.p.glcm_distance;
+        h.hx = (h.r + 3) / 4 * 4;
+        h.box_x = tune.brick_x + 2 * h.hx;
+        h.box_y = tune.brick_y + 2 * h.r;
+        h.box_z = tune.brick_z + 2 * h.r;
+        h.disc_mode = j.p.disc_mode;
+        h.bin_count = j.p.bin_count;
+        h.anchor_zero_floor = j.p.fbw_anchor == FR_ANCHOR_ZERO_FLOOR;
+        h.kurt_excess = j.p.kurtosis_excess ? 1 : 0;
+        h.nf = j.nf;
+        h.families = j.families;
+        h.bin_width = j.p.bin_width;
+        h.voxel_volume = j.p.spacing[0] * j.p.spacing[1] * j.p.spacing[2];
+        memcpy(h.row_of, j.row_of, sizeof(h.row_of));
+        cuuint64_t gdim[3] = {(cuuint64_t)j.px, (cuuint64_t)j.p.ny, (cuuint64_t)j.p.nz};
+        cuuint64_t gstride[2] = {(cuuint64_t)j.px * 4, (cuuint64_t)j.px * j.p.ny * 4};
+        cuuint32_t box[3] = {(cuuint32_t)h.box_x, (cuuint32_t)h.box_y, (cuuint32_t)h.box_z};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult cr = enc(&h.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, (void*)j.packed, gdim,
+                          gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) throw CudaFail{FR_ERR_UNSUPPORTED};
+      }
+      jobs_dev = dev_alloc<FrJob>(jobs.size(), &bytes);
+      FR_TRY(cudaMemcpyAsync(jobs_dev, hjobs.data(), jobs.size() * sizeof(FrJob),
+                             cudaMemcpyHostToDevice, s));
+      // items: most expensive windows first, then job, then brick order
+      std::vector<FrItem> all;
+      std::vector<int> order(jobs.size());
+      for (size_t i = 0; i < jobs.size(); ++i) order[i] = (int)i;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return jobs[a].p.kernel_radius > jobs[b].p.kernel_radius;
+      });
+      for (int i : order)
+        for (FrItem it : jobs[i].items) {
+          it.job = i;
+          all.push_back(it);
+        }
+      n_items = (int)all.size();
+      items_dev = dev_alloc<FrItem>(all.size(), &bytes);
+      FR_TRY(cudaMemcpyAsync(items_dev, all.data(), all.size() * sizeof(FrItem),
+                             cudaMemcpyHostToDevice, s));
+      run_ptrs_dev = dev_alloc<void*>(2 * jobs.size(), &bytes);
+      queue = dev_alloc<uint32_t>(1, &bytes);
+      status = dev_alloc<int32_t>(1, &bytes);
+      FR_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
+      FR_TRY(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+      FR_TRY(cudaEventCreate(&k_begin));
+      FR_TRY(cudaEventCreate(&k_end));
+      FR_TRY(cudaStreamSynchronize(s));
+      for (auto& j : jobs) bytes += j.bytes;
+    } catch (CudaFail& f) {
+      cudaStreamSynchronize(s);
+      return f.st;
+    }
+    return FR_OK;
+  }
+
+  cudaError_t enqueue(cudaStream_t s) {
+    cudaError_t e = fr_launch_prepare(jobs_dev, (int)jobs.size(), max_voi, run_ptrs_dev, queue,
+                                      status, sms, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(k_begin, s)) != cudaSuccess) return e;
+    if ((e = fr_map_launch(false, args(false), grid, smem, s)) != cudaSuccess) return e;
+    return cudaEventRecord(k_end, s);
+  }
+
+  fr_status kernel_ms(float* ms) {
+    if (!ms) return FR_ERR_INVALID_ARG;
+    if (!ran) return FR_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return FR_ERR_CUDA;
+    if (cudaEventSynchronize(k_end) != cudaSuccess) return FR_ERR_CUDA;
+    return cudaEventElapsedTime(ms, k_begin, k_end) == cudaSuccess ? FR_OK : FR_ERR_CUDA;
+  }
+
+  fr_status capture_graph() {
+    if (gexec) return FR_OK;
+    if (!private_stream &&
+        cudaStreamCreateWithFlags(&private_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return FR_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(private_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return FR_ERR_CUDA;
+    cudaError_t e = enqueue(private_stream);
+    cudaError_t e2 = cudaStreamEndCapture(private_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      return FR_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&gexec, g, 0);
+    cudaGraphDestroy(g);
+    return e == cudaSuccess ? FR_OK : FR_ERR_CUDA;
+  }
+
+  fr_status run(void* const* ptrs, cudaStream_t s, bool graph) {
+    if (cudaSetDevice(device) != cudaSuccess) return FR_ERR_CUDA;
+    if (cudaMemcpyAsync(run_ptrs_dev, ptrs, 2 * jobs.size() * sizeof(void*),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return FR_ERR_CUDA;
+    if (graph) {
+      fr_status st = capture_graph();
+      if (st != FR_OK) return st;
+      if (cudaGraphLaunch(gexec, s) != cudaSuccess) return FR_ERR_CUDA;
+    } else {
+      if (enqueue(s) != cudaSuccess) return FR_ERR_CUDA;
+    }
+    if (cudaEventRecord(done, s) != cudaSuccess) return FR_ERR_CUDA;
+    ran = true;
+    return FR_OK;
+  }
+
+  fr_status sync_status() {
+    if (cudaSetDevice(device) != cudaSuccess) return FR_ERR_CUDA;
+    if (ran && cudaEventSynchronize(done) != cudaSuccess) return FR_ERR_CUDA;
+    int32_t st = 0;
+    if (cudaMemcpy(&st, status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return FR_ERR_CUDA;
+    if (st) return (fr_status)st;
+    for (auto& j : jobs) {
+      FrJobState js;
+      if (cudaMemcpy(&js, j.state, sizeof(js), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FR_ERR_CUDA;
+      if (js.status) return (fr_status)js.status;
+    }
+    return FR_OK;
+  }
+};
+
+fr_status engine_open(Engine& E, const fr_map_params* ps, const uint8_t* const* masks, int n,
+                      const fr_tune* tune) {
+  for (int i = 0; i < n; ++i) {
+    if (!valid_params(&ps[i]) || !masks[i]) return FR_ERR_INVALID_ARG;
+    if (ps[i].device != ps[0].device) return FR_ERR_INVALID_ARG;
+  }
+  E.tune = default_tune(tune);
+  if (!valid_tune(E.tune)) return FR_ERR_INVALID_ARG;
+  E.device = ps[0].device;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || E.device < 0 || E.device >= ndev)
+    return FR_ERR_UNSUPPORTED;
+  if (cudaSetDevice(E.device) != cudaSuccess) return FR_ERR_CUDA;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, E.device) != cudaSuccess) return FR_ERR_CUDA;
+  if (prop.major != 10 || prop.minor != 3) return FR_ERR_UNSUPPORTED;
+  E.sms = prop.multiProcessorCount;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return FR_ERR_CUDA;
+  fr_status st = FR_OK;
+  E.jobs.resize(n);
+  for (int i = 0; i < n && st == FR_OK; ++i) st = build_job(&ps[i], masks[i], E.tune, E.jobs[i], s);
+  if (st == FR_OK) st = E.finalize(s);
+  cudaStreamDestroy(s);
+  if (st != FR_OK) E.release();
+  return st;
+}
+
+}  // namespace
+
+struct fr_plan {
+  Engine E;
+  int16_t* img_stage = nullptr;
+  float* out_stage = nullptr;
+  size_t stage_bytes = 0;
+};
+
+struct fr_batch {
+  Engine E;
+};
+
+extern "C" {
+
+void fr_map_params_init(fr_map_params* p, int32_t nx, int32_t ny, int32_t nz) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->nx = nx;
+  p->ny = ny;
+  p->nz = nz;
+  p->spacing[0] = p->spacing[1] = p->spacing[2] = 1.0;
+  p->disc_mode = FR_FBN;
+  p->bin_count = 16;
+  p->bin_width = 25.0;
+  p->fbw_anchor = FR_ANCHOR_VOI_MIN;
+  p->kernel_radius = 1;
+  p->glcm_distance = 1;
+  p->feature_mask[0] = ~0ull;
+  p->feature_mask[1] = (1ull << (kNumFeatures - 64)) - 1ull;
+  p->kurtosis_excess = 1;
+  p->device = 0;
+  p->mask_on_device = 0;
+  p->reserved = 0;
+}
+
+fr_status fr_map_plan(const fr_map_params* p, const uint8_t* mask, const fr_tune* tune,
+                      fr_plan** out) {
+  if (!out) return FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!p || !mask) return FR_ERR_INVALID_ARG;
+  fr_plan* plan = new (std::nothrow) fr_plan();
+  if (!plan) return FR_ERR_OOM;
+  const uint8_t* masks[1] = {mask};
+  fr_status st = engine_open(plan->E, p, masks, 1, tune);
+  if (st != FR_OK) {
+    delete plan;
+    return st;
+  }
+  *out = plan;
+  return FR_OK;
+}
+
+fr_status fr_map_run(fr_plan* plan, const int16_t* image, float* out, fr_stream_t s) {
+  if (!plan || !image || !out) return FR_ERR_INVALID_ARG;
+  void* ptrs[2] = {(void*)image, (void*)out};
+  return plan->E.run(ptrs, (cudaStream_t)s, false);
+}
+
+fr_status fr_map_run_host(fr_plan* plan, const int16_t* image_host, float* out_host,
+                          fr_stream_t s) {
+  if (!plan || !image_host || !out_host) return FR_ERR_INVALID_ARG;
+  Engine& E = plan->E;
+  JobRes& j = E.jobs[0];
+  const size_t img_bytes = (size_t)j.p.nx * j.p.ny * j.p.nz * sizeof(int16_t);
+  const size_t out_bytes = (size_t)j.nf * j.n_voi * sizeof(float);
+  if (cudaSetDevice(E.device) != cudaSuccess) return FR_ERR_CUDA;
+  if (!plan->img_stage) {
+    if (cudaMalloc(&plan->img_stage, img_bytes) != cudaSuccess) return FR_ERR_OOM;
+    if (cudaMalloc(&plan->out_stage, out_bytes) != cudaSuccess) return FR_ERR_OOM;
+    plan->stage_bytes = img_bytes + out_bytes;
+  }
+  cudaStream_t cs = (cudaStream_t)s;
+  if (cudaMemcpyAsync(plan->img_stage, image_host, img_bytes, cudaMemcpyHostToDevice, cs) !=
+      cudaSuccess)
+    return FR_ERR_CUDA;
+  void* ptrs[2] = {(void*)plan->img_stage, (void*)plan->out_stage};
+  fr_status st = E.run(ptrs, cs, false);
+  if (st != FR_OK) return st;
+  if (cudaMemcpyAsync(out_host, plan->out_stage, out_bytes, cudaMemcpyDeviceToHost, cs) !=
+      cudaSuccess)
+    return FR_ERR_CUDA;
+  if (cudaStreamSynchronize(cs) != cudaSuccess) return FR_ERR_CUDA;
+  return E.sync_status();
+}
+
+fr_status fr_map_sync_status(fr_plan* plan) {
+  if (!plan) return FR_ERR_INVALID_ARG;
+  return plan->E.sync_status();
+}
+
+fr_status fr_plan_query(const fr_plan* plan, int64_t* n_voi, int32_t* n_rows,
+                        size_t* device_bytes) {
+  if (!plan) return FR_ERR_INVALID_ARG;
+  if (n_voi) *n_voi = plan->E.jobs[0].n_voi;
+  if (n_rows) *n_rows = plan->E.jobs[0].nf;
+  if (device_bytes) *device_bytes = plan->E.bytes + plan->stage_bytes;
+  return FR_OK;
+}
+
+fr_status fr_plan_voxel_index(const fr_plan* plan, int32_t* idx, fr_stream_t s) {
+  if (!plan || !idx) return FR_ERR_INVALID_ARG;
+  const JobRes& j = plan->E.jobs[0];
+  if (cudaSetDevice(plan->E.device) != cudaSuccess) return FR_ERR_CUDA;
+  return cudaMemcpyAsync(idx, j.voi, j.n_voi * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                         (cudaStream_t)s) == cudaSuccess
+             ? FR_OK
+             : FR_ERR_CUDA;
+}
+
+fr_status fr_plan_levels(fr_plan* plan, uint8_t* levels, int32_t* ng, int32_t* xmin,
+                         int32_t* xmax) {
+  if (!plan) return FR_ERR_INVALID_ARG;
+  Engine& E = plan->E;
+  const JobRes& j = E.jobs[0];
+  if (cudaSetDevice(E.device) != cudaSuccess) return FR_ERR_CUDA;
+  if (E.ran && cudaEventSynchronize(E.done) != cudaSuccess) return FR_ERR_CUDA;
+  if (levels) {
+    if (fr_launch_levels(j.packed, j.p.nx, j.p.ny * j.p.nz, j.px, levels, 0) != cudaSuccess)
+      return FR_ERR_CUDA;
+    if (cudaStreamSynchronize(0) != cudaSuccess) return FR_ERR_CUDA;
+  }
+  FrJobState js;
+  if (cudaMemcpy(&js, j.state, sizeof(js), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FR_ERR_CUDA;
+  if (ng) *ng = js.ng;
+  if (xmin) *xmin = js.xmin;
+  if (xmax) *xmax = js.xmax;
+  return FR_OK;
+}
+
+fr_status fr_scatter_dense(const fr_plan* plan, const float* out, float* dense, fr_stream_t s) {
+  if (!plan || !out || !dense) return FR_ERR_INVALID_ARG;
+  const JobRes& j = plan->E.jobs[0];
+  if (cudaSetDevice(plan->E.device) != cudaSuccess) return FR_ERR_CUDA;
+  const int64_t nvox = (int64_t)j.p.nx * j.p.ny * j.p.nz;
+  return fr_launch_scatter(j.voi, j.n_voi, j.nf, nvox, out, dense, (cudaStream_t)s) ==
+                 cudaSuccess
+             ? FR_OK
+             : FR_ERR_CUDA;
+}
+
+int64_t fr_debug_record_ints(const fr_plan* plan, int32_t ng) {
+  if (!plan || ng < 1 || ng > 255) return 0;
+  const int s = 2 * plan->E.jobs[0].p.kernel_radius + 1;
+  const int64_t w = (int64_t)s * s * s;
+  int64_t n = 4 + ng + (int64_t)kNumDirs * ng * ng + (int64_t)kNumDirs * ng * s + ng * w +
+              (int64_t)ng * 27 + ng;
+  n = (n + 1) & ~1LL;
+  return n + 2LL * ng;
+}
+
+fr_status fr_debug_matrices(fr_plan* plan, const int16_t* image, const int32_t* cols,
+                            int32_t n, int32_t ng, int32_t* rec, fr_stream_t s) {
+  if (!plan || !image || !cols || n < 1 || !rec) return FR_ERR_INVALID_ARG;
+  Engine& E = plan->E;
+  JobRes& j = E.jobs[0];
+  for (int i = 0; i < n; ++i)
+    if (cols[i] < 0 || cols[i] >= j.n_voi) return FR_ERR_INVALID_ARG;
+  const int64_t stride = fr_debug_record_ints(plan, ng);
+  if (stride == 0) return FR_ERR_INVALID_ARG;
+  cudaStream_t cs = (cudaStream_t)s;
+  if (cudaSetDevice(E.device) != cudaSuccess) return FR_ERR_CUDA;
+  // discretise this image, then check its level count
+  void* ptrs[2] = {(void*)image, nullptr};
+  if (cudaMemcpyAsync(E.run_ptrs_dev, ptrs, sizeof(ptrs), cudaMemcpyHostToDevice, cs) !=
+      cudaSuccess)
+    return FR_ERR_CUDA;
+  if (fr_launch_prepare(E.jobs_dev, 1, E.max_voi, E.run_ptrs_dev, E.queue, E.status, E.sms,
+                        cs) != cudaSuccess)
+    return FR_ERR_CUDA;
+  FrJobState js;
+  if (cudaMemcpyAsync(&js, j.state, sizeof(js), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+      cudaStreamSynchronize(cs) != cudaSuccess)
+    return FR_ERR_CUDA;
+  if (js.status) return (fr_status)js.status;
+  if (js.ng != ng) return FR_ERR_MISMATCH;
+  // one item per requested column, in a job copy whose column list is cols
+  std::vector<int32_t> voi(j.n_voi);
+  if (cudaMemcpy(voi.data(), j.voi, j.n_voi * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return FR_ERR_CUDA;
+  std::vector<FrItem> items(n);
+  for (int i = 0; i < n; ++i) {
+    const int lin = voi[cols[i]];
+    const int x = lin % j.p.nx, y = (lin / j.p.nx) % j.p.ny, z = lin / (j.p.nx * j.p.ny);
+    items[i].job = 0;
+    items[i].bx = x / E.tune.brick_x * E.tune.brick_x;
+    items[i].by = y / E.tune.brick_y * E.tune.brick_y;
+    items[i].bz = z / E.tune.brick_z * E.tune.brick_z;
+    items[i].j0 = i;
+    items[i].n = 1;
+  }
+  FrJob hj = E.hjobs[0];
+  FrJob* djob = nullptr;
+  FrItem* ditems = nullptr;
+  int32_t* dcols = nullptr;
+  fr_status st = FR_OK;
+  do {
+    if (cudaMalloc(&djob, sizeof(FrJob)) != cudaSuccess ||
+        cudaMalloc(&ditems, n * sizeof(FrItem)) != cudaSuccess ||
+        cudaMalloc(&dcols, n * sizeof(int32_t)) != cudaSuccess) {
+      st = FR_ERR_OOM;
+      break;
+    }
+    hj.bcols = dcols;
+    if (cudaMemcpyAsync(djob, &hj, sizeof(FrJob), cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaMemcpyAsync(ditems, items.data(), n * sizeof(FrItem), cudaMemcpyHostToDevice, cs) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(dcols, cols, n * sizeof(int32_t), cudaMemcpyHostToDevice, cs) !=
+            cudaSuccess ||
+        cudaMemsetAsync(rec, 0, (size_t)n * stride * sizeof(int32_t), cs) != cudaSuccess ||
+        cudaMemsetAsync(E.queue, 0, sizeof(uint32_t), cs) != cudaSuccess) {
+      st = FR_ERR_CUDA;
+      break;
+    }
+    // the output pointer of the debug run is a scratch buffer
+    float* scratch = nullptr;
+    if (cudaMalloc(&scratch, (size_t)j.nf * j.n_voi * sizeof(float)) != cudaSuccess) {
+      st = FR_ERR_OOM;
+      break;
+    }
+    void* ptrs2[2] = {(void*)image, (void*)scratch};
+    FrMapArgs a = E.args(true);
+    a.jobs = djob;
+    a.items = ditems;
+    a.n_items = n;
+    a.dbg = rec;
+    a.dbg_stride = stride;
+    if (cudaMemcpyAsync(E.run_ptrs_dev, ptrs2, sizeof(ptrs2), cudaMemcpyHostToDevice, cs) !=
+            cudaSuccess ||
+        fr_map_launch(true, a, std::min(E.grid, n), E.smem, cs) != cudaSuccess ||
+        cudaStreamSynchronize(cs) != cudaSuccess)
+      st = FR_ERR_CUDA;
+    cudaFree(scratch);
+  } while (0);
+  cudaFree(djob);
+  cudaFree(ditems);
+  cudaFree(dcols);
+  if (st != FR_OK) return st;
+  int32_t dst = 0;
+  if (cudaMemcpy(&dst, E.status, sizeof(dst), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FR_ERR_CUDA;
+  return (fr_status)dst;
+}
+
+fr_status fr_plan_last_kernel_ms(fr_plan* plan, float* ms) {
+  if (!plan) return FR_ERR_INVALID_ARG;
+  return plan->E.kernel_ms(ms);
+}
+
+fr_status fr_batch_last_kernel_ms(fr_batch* b, float* ms) {
+  if (!b) return FR_ERR_INVALID_ARG;
+  return b->E.kernel_ms(ms);
+}
+
+void fr_map_destroy(fr_plan* plan) {
+  if (!plan) return;
+  cudaSetDevice(plan->E.device);
+  plan->E.release();
+  cudaFree(plan->img_stage);
+  cudaFree(plan->out_stage);
+  delete plan;
+}
+
+fr_status fr_batch_plan(const fr_map_params* params, const uint8_t* const* masks, int32_t n,
+                        const fr_tune* tune, fr_batch** out) {
+  if (!out) return FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!params || !masks || n < 1) return FR_ERR_INVALID_ARG;
+  fr_batch* b = new (std::nothrow) fr_batch();
+  if (!b) return FR_ERR_OOM;
+  fr_status st = engine_open(b->E, params, masks, n, tune);
+  if (st != FR_OK) {
+    delete b;
+    return st;
+  }
+  *out = b;
+  return FR_OK;
+}
+
+fr_status fr_batch_query(const fr_batch* b, int32_t i, int64_t* n_voi, int32_t* n_rows) {
+  if (!b || i < 0 || i >= (int32_t)b->E.jobs.size()) return FR_ERR_INVALID_ARG;
+  if (n_voi) *n_voi = b->E.jobs[i].n_voi;
+  if (n_rows) *n_rows = b->E.jobs[i].nf;
+  return FR_OK;
+}
+
+fr_status fr_batch_run(fr_batch* b, const int16_t* const* images, float* const* outs,
+                       fr_stream_t s) {
+  if (!b || !images || !outs) return FR_ERR_INVALID_ARG;
+  const size_t n = b->E.jobs.size();
+  std::vector<void*> ptrs(2 * n);
+  for (size_t i = 0; i < n; ++i) {
+    if (!images[i] || !outs[i]) return FR_ERR_INVALID_ARG;
+    ptrs[2 * i] = (void*)images[i];
+    ptrs[2 * i + 1] = (void*)outs[i];
+  }
+  return b->E.run(ptrs.data(), (cudaStream_t)s, true);
+}
+
+fr_status fr_batch_sync_status(fr_batch* b) {
+  if (!b) return FR_ERR_INVALID_ARG;
+  return b->E.sync_status();
+}
+
+void fr_batch_destroy(fr_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->E.device);
+  b->E.release();
+  delete b;
+}
+
+int32_t fr_feature_count(void) { return kNumFeatures; }
+
+const char* fr_feature_name(int32_t id) {
+  return (id >= 0 && id < kNumFeatures) ? kFeatureNames[id] : nullptr;
+}
+
+const char* fr_status_string(fr_status s) {
+  switch (s) {
+    case FR_OK: return "ok";
+    case FR_ERR_INVALID_ARG: return "invalid argument";
+    case FR_ERR_EMPTY_MASK: return "empty mask";
+    case FR_ERR_TOO_MANY_LEVELS: return "more than 255 gray levels";
+    case FR_ERR_OOM: return "out of memory";
+    case FR_ERR_CUDA: return "CUDA error";
+    case FR_ERR_TIMEOUT: return "device wait timed out";
+    case FR_ERR_UNSUPPORTED: return "unsupported device or size";
+    case FR_ERR_MISMATCH: return "arguments disagree with the plan";
+  }
+  return "unknown status";
+}
+
+fr_status fr_direction(int32_t i, int32_t* dz, int32_t* dy, int32_t* dx) {
+  if (i < 0 || i >= kNumDirs || !dz || !dy || !dx) return FR_ERR_INVALID_ARG;
+  *dz = kDirs[i][0];
+  *dy = kDirs[i][1];
+  *dx = kDirs[i][2];
+  return FR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// fr_internal.h -- structures shared by the host plan code and the kernels.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda.h>
+
+namespace fr {
+
+constexpr int kNumFeatures = 93;
+constexpr int kNumDirs = 13;
+constexpr int kMaxRadius = 7;
+// Present-level count and level-range limits of the per-warp shared-memory
+// arena; a voxel whose window exceeds either uses the warp's global slab.
+constexpr int kMCap = 24;
+constexpr int kBinCap = 64;
+// GLCM MCC: directions whose present-level count is at most kCapL are solved
+// after the 13-direction loop, one lane per direction, from packed matrices
+// kept in per-direction slots of kSlot floats (packed upper triangle of
+// kCapL levels, then 3 scratch vectors; odd size spreads the banks).
+constexpr int kCapL = 12;
+constexpr int kSlot = kCapL * (kCapL + 1) / 2 + 3 * kCapL + 1;
+constexpr int kMaxConsumerWarps = 16;
+constexpr int kMaxStages = 4;
+
+// Feature families (bits of FrJob::families).
+enum : uint32_t {
+  kFamFO = 1u << 0,
+  kFamGLCM = 1u << 1,
+  kFamMCC = 1u << 2,  // GLCM MCC (the eigenvalue part) requested
+  kFamGLRLM = 1u << 3,
+  kFamGLSZM = 1u << 4,
+  kFamGLDM = 1u << 5,
+  kFamNGTDM = 1u << 6,
+};
+
+// Run-time state of a job, written by the preparation kernels.
+struct FrJobState {
+  int32_t xmin, xmax;  // VOI intensity range
+  int32_t ng;          // gray levels of the discretisation
+  int32_t status;      // fr_status of the job (0 = ok)
+};
+
+// One VOI to map (device-resident; 128-byte aligned for the tensor map).
+struct alignas(128) FrJob {
+  CUtensorMap tmap;      // 3-D tiled map over `packed` (uint32, [nz][ny][px])
+  uint32_t* packed;      // ((raw + 32768) << 8) | level, 0 outside the VOI
+  const int32_t* voi;    // linear voxel index per output column
+  const int32_t* bcols;  // output columns ordered by brick
+  FrJobState* state;
+  int64_t n_voi;
+  int32_t nx, ny, nz, px;
+  int32_t r, delta;
+  int32_t hx;  // x halo of the TMA box (multiple of 4, >= r)
+  int32_t box_x, box_y, box_z;
+  int32_t disc_mode, bin_count, anchor_zero_floor;
+  int32_t kurt_excess;
+  int32_t nf;  // output rows
+  uint32_t families;
+  double bin_width;
+  double voxel_volume;
+  int16_t row_of[96];  // output row of each feature id, -1 if not selected
+};
+
+// One work-queue entry: up to `n` voxels of one brick of one job.
+struct FrItem {
+  int32_t job;
+  int32_t bx, by, bz;  // brick origin (voxels)
+  int32_t j0, n;       // range in the job's brick-ordered column list
+};
+
+// Byte offsets of one warp's shared-memory arena.
+struct FrArena {
+  int32_t bytes;      // arena size (multiple of 16)
+  int32_t off_kb;     // uint32[p_max]   sort keys / zone keys
+  int32_t off_lvl;    // uint8[w_max]    compact level + 1 per window position
+  int32_t off_lut;    // uint8[256]      level -> compact index
+  int32_t off_lev;    // uint8[256]      compact index -> level
+  int32_t off_st;     // uint16[264]     start of each level run in the sorted keys
+  int32_t off_fv;     // float[96]       features of the current voxel
+  int32_t off_acc;    // float[32] + int32[32]  per-direction accumulators
+  int32_t off_tmp;    // float[64]       per-direction scratch
+  int32_t off_big;    // family matrices (layout from (mc, bc, w))
+  int32_t big_bytes;  // size of the shared big region
+  int32_t p_max, w_max;
+};
+
+// Per-run pointers of job j: run_ptrs[2j] = image (int16), run_ptrs[2j+1] =
+// output (float32 [nf][n_voi]).
+struct FrMapArgs {
+  const FrJob* jobs;
+  void* const* run_ptrs;
+  const FrItem* items;
+  int32_t n_items;
+  int32_t consumer_warps;
+  int32_t stages;
+  int32_t tile_bytes;  // per stage, multiple of 128
+  uint32_t* queue;     // work-queue head (reset per run)
+  int32_t* status;     // launch-wide status word (timeouts)
+  char* slab;          // global big regions, one per resident warp
+  int64_t slab_stride; // bytes per warp
+  int32_t slab_ngc;    // level cap the slab is laid out for
+  FrArena arena;
+  int32_t* dbg;        // debug records (DUMP kernel only)
+  int64_t dbg_stride;  // int32 per record
+  int64_t timeout_ns;  // bound of every device wait
+};
+
+// Big-region layout for caps (mc, bc) and window size w.
+struct BigLayout {
+  int32_t cnt, marg, prank, sbin, dbin, vec;  // GLCM (vec: 4 float vectors of mc)
+  int32_t mn, mres, slots;                    // GLCM MCC: n per direction, results, slots
+  int32_t rhist, rlv, rlen;                  // GLRLM
+  int32_t parent, zsz, zlv;                  // GLSZM
+  int32_t ghist, gj, ngn, ngs;               // GLDM / NGTDM
+  int32_t bytes;
+};
+
+__host__ __device__ inline int32_t fr_align(int32_t v, int32_t a) {
+  return (v + a - 1) / a * a;
+}
+
+__host__ __device__ inline BigLayout fr_big_layout(int32_t mc, int32_t bc,
+                                                   int32_t w) {
+  BigLayout L;
+  // GLCM
+  L.cnt = 0;
+  L.marg = L.cnt + mc * mc * 4;
+  L.prank = L.marg + mc * 4;
+  L.sbin = L.prank + mc * 4;
+  L.dbin = L.sbin + 2 * bc * 4;
+  L.vec = L.dbin + bc * 4;
+  L.mn = L.vec + 4 * mc * 4;
+  L.mres = L.mn + 16 * 4;
+  L.slots = L.mres + 16 * 4;
+  int32_t glcm_end = L.slots + kNumDirs * kSlot * 4;
+  // GLRLM
+  L.rhist = 0;
+  L.rlv = L.rhist + mc * 16 * 4;
+  L.rlen = L.rlv + mc * 4;
+  int32_t glrlm_end = L.rlen + 16 * 4;
+  // GLSZM
+  L.parent = 0;
+  L.zsz = L.parent + w * 4;
+  L.zlv = L.zsz + w * 4;
+  int32_t glszm_end = L.zlv + mc * 4;
+  // GLDM + NGTDM
+  L.ghist = 0;
+  L.gj = L.ghist + mc * 28 * 4;
+  L.ngn = L.gj + 28 * 4;
+  L.ngs = fr_align(L.ngn + mc * 4, 8);
+  int32_t gldm_end = L.ngs + mc * 8;
+  int32_t m = glcm_end;
+  if (glrlm_end > m) m = glrlm_end;
+  if (glszm_end > m) m = glszm_end;
+  if (gldm_end > m) m = gldm_end;
+  L.bytes = fr_align(m, 16);
+  return L;
+}
+
+inline int32_t fr_next_pow2(int32_t v) {
+  int32_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Arena layout for windows up to radius r_max.
+inline FrArena fr_make_arena(int32_t r_max) {
+  FrArena a;
+  const int32_t s = 2 * r_max + 1;
+  a.w_max = s * s * s;
+  a.p_max = fr_next_pow2(a.w_max);
+  int32_t o = 0;
+  a.off_kb = o;
+  o += a.p_max * 4;
+  a.off_lvl = o;
+  o += fr_align(a.w_max, 16);
+  a.off_lut = o;
+  o += 256;
+  a.off_lev = o;
+  o += 256;
+  a.off_st = o;
+  o += 264 * 2;
+  a.off_fv = o;
+  o += 96 * 4;
+  a.off_acc = o;
+  o += 64 * 4;
+  a.off_tmp = o;
+  o += 64 * 4;
+  a.off_big = fr_align(o, 16);
+  BigLayout L = fr_big_layout(kMCap, kBinCap, a.w_max);
+  a.big_bytes = L.bytes;
+  a.bytes = fr_align(a.off_big + a.big_bytes, 16);
+  return a;
+}
+
+}  // namespace fr

@@ -1,0 +1,276 @@
+// fr_map_kernel.cu -- the persistent mapping kernel.
+//
+// One CTA = 1 producer warp + NW consumer warps, resident for the whole
+// launch.  The producer pops work items (up to N voxels of one brick of one
+// VOI) from a device queue and stages each brick's halo -- a 3-D box of the
+// packed level/intensity volume -- into shared memory with one TMA tiled
+// load completing on an mbarrier; `stages` buffers let it run ahead.  Each
+// consumer warp maps whole voxels (fr_voxel.cuh) from the staged tile and
+// releases the buffer through a second mbarrier.  Every wait is bounded in
+// time; a wait that runs out records FR_ERR_TIMEOUT and the CTA leaves after
+// its own copies have landed.
+#include <cstdint>
+
+#include "fr_device.cuh"
+#include "fr_internal.h"
+#include "fr_voxel.cuh"
+
+namespace fr {
+
+constexpr int kStatusTimeout = 6;      // FR_ERR_TIMEOUT
+constexpr int kStatusUnsupported = 7;  // FR_ERR_UNSUPPORTED
+
+// Shared-memory layout of a CTA (host and device agree through this).
+struct CtaLayout {
+  int32_t tiles, bars, slots, arenas, bytes;
+};
+
+__host__ __device__ inline CtaLayout fr_cta_layout(int stages, int tile_bytes,
+                                                   int nw, int arena_bytes) {
+  CtaLayout c;
+  c.tiles = 0;
+  c.bars = stages * tile_bytes;
+  c.slots = c.bars + 2 * stages * 8;
+  c.arenas = fr_align(c.slots + stages * 4, 128);
+  c.bytes = c.arenas + nw * arena_bytes;
+  return c;
+}
+
+template <bool DUMP>
+__device__ void map_voxel(const FrMapArgs& args, const FrJob& job,
+                          const FrItem& item, const uint32_t* tile, int col,
+                          Arena& A, char* smem_big, char* slab_big, int it) {
+  const int lane = lane_id();
+  const int lin = job.voi[col];
+  const int x = lin % job.nx;
+  const int y = (lin / job.nx) % job.ny;
+  const int z = lin / (job.nx * job.ny);
+  Win w;
+  w.r = job.r;
+  w.s = 2 * job.r + 1;
+  w.s2 = w.s * w.s;
+  w.W = w.s2 * w.s;
+  w.ms.init((unsigned)w.s);
+  w.ms2.init((unsigned)w.s2);
+  w.ng = job.state->ng;
+  const int cx = (x - job.r) - (item.bx - job.hx);
+  const int cy = y - item.by;
+  const int cz = z - item.bz;
+  w.nv = gather_window(w, A, tile, job.box_x, job.box_y, cx, cy, cz);
+  warp_sort(A.kb, w.nv);
+
+  int32_t* rec = nullptr;
+  int32_t *d_hist = nullptr, *d_glcm = nullptr, *d_glrlm = nullptr,
+          *d_glszm = nullptr, *d_gldm = nullptr, *d_ngn = nullptr;
+  long long* d_ngs = nullptr;
+  if (DUMP) {
+    const int ng = w.ng;
+    rec = args.dbg + (size_t)it * args.dbg_stride;
+    d_hist = rec + 4;
+    d_glcm = d_hist + ng;
+    d_glrlm = d_glcm + (size_t)kNumDirs * ng * ng;
+    d_glszm = d_glrlm + (size_t)kNumDirs * ng * w.s;
+    d_gldm = d_glszm + (size_t)ng * w.W;
+    d_ngn = d_gldm + (size_t)ng * 27;
+    size_t o = (size_t)(d_ngn + ng - rec);
+    o = (o + 1) & ~(size_t)1;
+    d_ngs = (long long*)(rec + o);
+    if (lane == 0) {
+      rec[0] = ng;
+      rec[1] = w.s;
+      rec[2] = w.W;
+      rec[3] = w.nv;
+    }
+  }
+
+  first_order(w, A, job, d_hist);
+  compact_levels(w, A);
+  if (w.m > kMCap || w.R >= kBinCap) {
+    if (slab_big == nullptr) {
+      if (lane == 0) atomicCAS(args.status, 0, kStatusUnsupported);
+      for (int f = lane; f < kNumFeatures; f += 32) A.fv[f] = kNaNf;
+      __syncwarp();
+      goto store;
+    }
+    A.big = slab_big;
+    A.mc = args.slab_ngc;
+    A.bc = args.slab_ngc;
+  } else {
+    A.big = smem_big;
+    A.mc = kMCap;
+    A.bc = kBinCap;
+  }
+  A.L = fr_big_layout(A.mc, A.bc, w.W);
+  if (job.families & kFamGLCM) glcm_family(w, A, job, d_glcm);
+  if (job.families & kFamGLRLM) glrlm_family(w, A, d_glrlm);
+  if (job.families & kFamGLSZM) glszm_family(w, A, d_glszm);
+  if (job.families & (kFamGLDM | kFamNGTDM))
+    gldm_ngtdm_family(w, A, job, d_gldm, d_ngn, d_ngs);
+store:
+  __syncwarp();
+  float* out = (float*)args.run_ptrs[2 * item.job + 1];
+  for (int f = lane; f < kNumFeatures; f += 32) {
+    const int row = job.row_of[f];
+    if (row >= 0) out[(size_t)row * job.n_voi + col] = A.fv[f];
+  }
+  __syncwarp();
+}
+
+template <bool DUMP>
+__global__ void __launch_bounds__(32 * (kMaxConsumerWarps + 1), 1)
+    fr_map_kernel(const __grid_constant__ FrMapArgs args) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int S = args.stages, NW = args.consumer_warps;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const CtaLayout cl = fr_cta_layout(S, args.tile_bytes, NW, args.arena.bytes);
+  uint64_t* full = (uint64_t*)(smem + cl.bars);
+  uint64_t* empty = full + S;
+  volatile int* slot = (volatile int*)(smem + cl.slots);
+  const volatile int* abort_flag = args.status;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NW);
+    }
+    fence_mbar_init();
+  }
+  if (warp < NW) {
+    // zero this warp's arena (the count matrices must start at zero)
+    uint4* a = (uint4*)(smem + cl.arenas + warp * args.arena.bytes);
+    for (int i = lane; i < args.arena.bytes / 16; i += 32) a[i] = make_uint4(0, 0, 0, 0);
+  }
+  __syncthreads();
+
+  if (warp == NW) {
+    // ---------------------------------------------------------- producer
+    if (lane != 0) return;
+    int stage = 0;
+    unsigned phase = 0;
+    bool issued[kMaxStages];
+    unsigned ipar[kMaxStages];
+    for (int s = 0; s < kMaxStages; ++s) {
+      issued[s] = false;
+      ipar[s] = 0;
+    }
+    const CUtensorMap* last = nullptr;
+    bool failed = false;
+    while (true) {
+      int it = (int)atomicAdd(args.queue, 1u);
+      if (it >= args.n_items) it = -1;
+      const FrItem* item = nullptr;
+      const FrJob* job = nullptr;
+      if (it >= 0) {
+        item = &args.items[it];
+        job = &args.jobs[item->job];
+        if (job->state->status != 0) continue;  // job failed in preparation
+      }
+      if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, args.timeout_ns, abort_flag)) {
+        atomicCAS(args.status, 0, kStatusTimeout);
+        failed = true;
+        break;
+      }
+      slot[stage] = it;
+      if (it < 0) {
+        mbar_arrive(&full[stage]);
+        break;
+      }
+      const CUtensorMap* tm = &job->tmap;
+      if (tm != last) {
+        tmap_acquire(tm);
+        last = tm;
+      }
+      const unsigned bytes = (unsigned)(job->box_x * job->box_y * job->box_z * 4);
+      mbar_arrive_expect_tx(&full[stage], bytes);
+      tma_load_3d(smem + cl.tiles + (size_t)stage * args.tile_bytes, tm,
+                  item->bx - job->hx, item->by - job->r, item->bz - job->r,
+                  &full[stage]);
+      issued[stage] = true;
+      ipar[stage] = phase;
+      if (++stage == S) {
+        stage = 0;
+        phase ^= 1u;
+      }
+    }
+    // On the normal path every issued copy is consumed (consumers wait for
+    // it) before the CTA can finish.  After a failed wait the consumers may
+    // be gone: leave only after this CTA's own copies have landed (the last
+    // phase of each stage is then the last issue, so its parity is exact).
+    if (failed) {
+      const int zero = 0;
+      for (int s = 0; s < S; ++s)
+        if (issued[s]) mbar_wait_bounded(&full[s], ipar[s], args.timeout_ns, &zero);
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------ consumers
+  unsigned char* ab = smem + cl.arenas + warp * args.arena.bytes;
+  Arena A;
+  A.kb = (uint32_t*)(ab + args.arena.off_kb);
+  A.lvl = ab + args.arena.off_lvl;
+  A.lut = ab + args.arena.off_lut;
+  A.lev = ab + args.arena.off_lev;
+  A.st = (uint16_t*)(ab + args.arena.off_st);
+  A.fv = (float*)(ab + args.arena.off_fv);
+  A.facc = (float*)(ab + args.arena.off_acc);
+  A.nacc = (int*)(ab + args.arena.off_acc + 32 * 4);
+  A.tmp = (float*)(ab + args.arena.off_tmp);
+  char* smem_big = (char*)(ab + args.arena.off_big);
+  char* slab_big = args.slab ? args.slab + ((size_t)blockIdx.x * NW + warp) * args.slab_stride
+                             : nullptr;
+  int stage = 0;
+  unsigned phase = 0;
+  while (true) {
+    if (!mbar_wait_bounded(&full[stage], phase, args.timeout_ns, abort_flag)) {
+      if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
+      break;
+    }
+    const int it = slot[stage];
+    if (it < 0) break;
+    const FrItem item = args.items[it];
+    const FrJob& job = args.jobs[item.job];
+    const uint32_t* tile = (const uint32_t*)(smem + cl.tiles + (size_t)stage * args.tile_bytes);
+    for (int t = warp; t < item.n; t += NW) {
+      const int col = job.bcols[item.j0 + t];
+      map_voxel<DUMP>(args, job, item, tile, col, A, smem_big, slab_big, it);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[stage]);
+    if (++stage == S) {
+      stage = 0;
+      phase ^= 1u;
+    }
+  }
+}
+
+}  // namespace fr
+
+// Host launch helpers (C++ linkage, used by fr_api.cu).
+namespace fr {
+
+int fr_map_smem_bytes(int stages, int tile_bytes, int nw, int arena_bytes) {
+  return fr_cta_layout(stages, tile_bytes, nw, arena_bytes).bytes;
+}
+
+cudaError_t fr_map_configure(bool dump, int smem_bytes) {
+  const void* fn = dump ? (const void*)fr_map_kernel<true> : (const void*)fr_map_kernel<false>;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+}
+
+cudaError_t fr_map_occupancy(bool dump, int threads, int smem_bytes, int* blocks) {
+  const void* fn = dump ? (const void*)fr_map_kernel<true> : (const void*)fr_map_kernel<false>;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, threads, smem_bytes);
+}
+
+cudaError_t fr_map_launch(bool dump, const FrMapArgs& args, int grid, int smem_bytes,
+                          cudaStream_t s) {
+  const int threads = 32 * (args.consumer_warps + 1);
+  if (dump)
+    fr_map_kernel<true><<<grid, threads, smem_bytes, s>>>(args);
+  else
+    fr_map_kernel<false><<<grid, threads, smem_bytes, s>>>(args);
+  return cudaGetLastError();
+}
+
+}  // namespace fr

@@ -1,0 +1,1344 @@
+// fr_voxel.cuh -- one warp maps one voxel: window gather, first-order
+// statistics, and the GLCM / GLRLM / GLSZM / GLDM / NGTDM matrices and
+// features of the sub-VOI V(v) = window(v) n VOI.
+//
+// Definitions (paper: spatial mapping evaluates each feature on the
+// neighbourhood of every VOI voxel; Table 2 lists the 93 features; the
+// backends follow the IBSI definitions):
+//   - window: cube of side s = 2r+1 around v (Chebyshev radius r), clipped
+//     to the image; positions outside the VOI carry level 0.
+//   - GLCM: 13 directions d, symmetric counts of pairs (u, u + delta*d),
+//     features per direction, mean over directions with pairs.
+//   - GLRLM: maximal equal-level runs inside V(v) along each direction,
+//     features per direction, mean over directions.
+//   - GLSZM: 26-connected equal-level zones inside V(v).
+//   - GLDM: alpha = 0, distance 1; dependence j = 1 + equal neighbours.
+//   - NGTDM: 26-neighbourhood inside V(v), voxels without a neighbour skipped.
+//
+// Numerics: every matrix count is an exact integer; every numerator that
+// can cancel (variances, correlation, cluster shade, skewness, kurtosis) is
+// an exact 32-, 64- or 128-bit integer; sums of nonnegative terms
+// (emphases, entropies as (c/N) log2(N/c)) accumulate in fp32; the final
+// ratios round once in fp32.
+//
+// Latency: a warp works on one voxel at a time, so the code avoids long
+// dependent chains -- integer sums use the single-instruction warp
+// reduction, float sums are reduced together, equal matrix keys are merged
+// with __match_any_sync before their shared-memory atomic, every
+// per-direction feature is finished by its own lane with one division, and
+// the 13 GLCM MCC eigenproblems of a voxel are solved concurrently, one lane
+// per direction.
+#pragma once
+
+#include <cstdint>
+
+#include "fr_device.cuh"
+#include "fr_internal.h"
+
+namespace fr {
+
+// (dz, dy, dx) of the 13 directions: the vectors of {-1,0,1}^3 that are
+// lexicographically greater than (0,0,0), in increasing order.
+__constant__ signed char c_dirs[13][3] = {
+    {0, 0, 1},  {0, 1, -1}, {0, 1, 0},  {0, 1, 1},  {1, -1, -1},
+    {1, -1, 0}, {1, -1, 1}, {1, 0, -1}, {1, 0, 0},  {1, 0, 1},
+    {1, 1, -1}, {1, 1, 0},  {1, 1, 1}};
+
+// L / w for w = 0..26 with L = lcm(1..26): s_i * L is then an exact
+// integer sum of |i*w - S| * (L / w).
+struct LdivTable {
+  long long v[27];
+};
+constexpr long long ct_gcd(long long a, long long b) {
+  return b == 0 ? a : ct_gcd(b, a % b);
+}
+constexpr long long ct_lcm_upto(int n) {
+  long long l = 1;
+  for (int k = 2; k <= n; ++k) l = l / ct_gcd(l, k) * k;
+  return l;
+}
+constexpr long long kLcm26 = ct_lcm_upto(26);
+constexpr LdivTable make_ldiv() {
+  LdivTable t{};
+  t.v[0] = 0;
+  for (int w = 1; w <= 26; ++w) t.v[w] = kLcm26 / w;
+  return t;
+}
+__constant__ LdivTable c_ldiv = make_ldiv();
+
+constexpr float kNaNf = __builtin_nanf("");
+
+// Per-voxel window geometry and level summary (warp-uniform).
+struct Win {
+  int r, s, s2, W;
+  Magic ms, ms2;
+  int nv;    // voxels in V(v)
+  int m;     // distinct levels present
+  int lev0;  // smallest present level
+  int R;     // largest - smallest present level
+  int ng;    // levels of the discretisation
+  long long u2;  // sum of squared level counts
+};
+
+// Per-warp pointers.
+struct Arena {
+  uint32_t* kb;
+  uint8_t* lvl;
+  uint8_t* lut;
+  uint8_t* lev;
+  uint16_t* st;  // run starts of the sorted keys
+  float* fv;
+  float* facc;
+  int* nacc;
+  float* tmp;
+  char* big;  // the selected big region
+  int mc, bc;
+  BigLayout L;
+};
+
+__device__ __forceinline__ void pos_to_zyx(const Win& w, int p, int& z, int& y,
+                                           int& x) {
+  z = (int)w.ms2.div((unsigned)p);
+  int rem = p - z * w.s2;
+  y = (int)w.ms.div((unsigned)rem);
+  x = rem - y * w.s;
+}
+
+__device__ __forceinline__ bool in_cube(const Win& w, int z, int y, int x) {
+  return (unsigned)z < (unsigned)w.s && (unsigned)y < (unsigned)w.s &&
+         (unsigned)x < (unsigned)w.s;
+}
+
+// ------------------------------------------------------------------ reductions
+// K float sums reduced together (independent butterflies interleave).
+template <int K>
+__device__ __forceinline__ void warp_sum_f32x(float (&v)[K]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(kFull, v[k], o);
+  }
+}
+
+__device__ __forceinline__ unsigned redux_u32(unsigned v) {
+  return __reduce_add_sync(kFull, v);
+}
+
+// Exact warp sum of nonnegative 64-bit values whose total is below 2^64:
+// four single-instruction reductions of 16-bit limbs.
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+  const unsigned l0 = __reduce_add_sync(kFull, (unsigned)(v & 0xffffu));
+  const unsigned l1 = __reduce_add_sync(kFull, (unsigned)((v >> 16) & 0xffffu));
+  const unsigned l2 = __reduce_add_sync(kFull, (unsigned)((v >> 32) & 0xffffu));
+  const unsigned l3 = __reduce_add_sync(kFull, (unsigned)(v >> 48));
+  return (unsigned long long)l0 + ((unsigned long long)l1 << 16) +
+         ((unsigned long long)l2 << 32) + ((unsigned long long)l3 << 48);
+}
+
+__device__ __forceinline__ float i128_to_f32(__int128 v) {
+  const bool neg = v < 0;
+  const unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const float f = (float)(unsigned long long)(u >> 64) * 18446744073709551616.0f +
+                  (float)(unsigned long long)u;
+  return neg ? -f : f;
+}
+
+// One quotient per lane; a zero denominator gives NaN.
+__device__ __forceinline__ float lane_quot(float num, float den) {
+  return den == 0.f ? kNaNf : num / den;
+}
+
+// ------------------------------------------------------------------ sorting
+// Ascending sort of n keys in a[0..n), padded to P = next power of two with
+// 0xffffffff.  Warp-synchronous bitonic network (registers for P <= 32).
+__device__ void warp_sort(uint32_t* a, int n) {
+  const int lane = lane_id();
+  int P = 1;
+  while (P < n) P <<= 1;
+  if (P <= 32) {
+    uint32_t x = lane < n ? a[lane] : 0xffffffffu;
+    for (int k = 2; k <= 32; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        uint32_t y = __shfl_xor_sync(kFull, x, j);
+        bool up = (lane & k) == 0;
+        bool lower = (lane & j) == 0;
+        uint32_t mn = x < y ? x : y, mx = x < y ? y : x;
+        x = (lower == up) ? mn : mx;
+      }
+    }
+    if (lane < P) a[lane] = x;
+    __syncwarp();
+    return;
+  }
+  for (int i = n + lane; i < P; i += 32) a[i] = 0xffffffffu;
+  __syncwarp();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < (P >> 1); i += 32) {
+        int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+        int hi = lo + j;
+        bool up = (lo & k) == 0;
+        uint32_t x = a[lo], y = a[hi];
+        if ((x > y) == up) {
+          a[lo] = y;
+          a[hi] = x;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// first index in a[lo..hi) with a[i] >= key (a sorted)
+__device__ __forceinline__ int lower_bound_u32(const uint32_t* a, int lo, int hi,
+                                               uint32_t key) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// (c/n) * log2(n/c) for 0 < c <= n
+__device__ __forceinline__ float ent_term(int c, int n) {
+  const float fc = (float)c, fn = (float)n;
+  return __fdividef(fc, fn) * log2f(__fdividef(fn, fc));
+}
+
+// ------------------------------------------------------------------ gather
+// Copy the window of the voxel at tile offset (cx, cy, cz) (window corner)
+// from the staged halo tile: kb[0..nv) receives the packed words of V(v)
+// (compacted), lvl[p] the gray level (0 outside V(v)).
+__device__ int gather_window(const Win& w, const Arena& A, const uint32_t* tile,
+                             int TX, int TY, int cx, int cy, int cz) {
+  const int lane = lane_id();
+  int nv = 0;
+  for (int base = 0; base < w.W; base += 32) {
+    int p = base + lane;
+    uint32_t word = 0;
+    if (p < w.W) {
+      int z, y, x;
+      pos_to_zyx(w, p, z, y, x);
+      word = tile[((cz + z) * TY + (cy + y)) * TX + (cx + x)];
+      A.lvl[p] = (uint8_t)(word & 0xffu);
+    }
+    unsigned b = __ballot_sync(kFull, word != 0u);
+    if (word != 0u) A.kb[nv + __popc(b & lanemask_lt())] = word;
+    nv += __popc(b);
+  }
+  __syncwarp();
+  return nv;
+}
+
+// ------------------------------------------------------------------ first order
+// Sorted keys -> the 18 first-order features, the present-level table
+// (lev, lut), m, lev0, R and the level-count square sum.
+__device__ void first_order(Win& w, const Arena& A, const FrJob& job,
+                            int32_t* dbg_hist) {
+  const int lane = lane_id();
+  const int N = w.nv;
+  const uint32_t* kb = A.kb;
+  auto xs = [&](int i) { return (int)(kb[i] >> 8) - 32768; };
+  // pass 1: sums and level-run starts
+  int s1 = 0;
+  unsigned long long s2 = 0;
+  int base = 0;
+  for (int c = 0; c < N; c += 32) {
+    int i = c + lane;
+    bool start = false;
+    int g = 0;
+    if (i < N) {
+      const uint32_t k = kb[i];
+      const int x = (int)(k >> 8) - 32768;
+      s1 += x;
+      s2 += (unsigned long long)((long long)x * x);
+      g = (int)(k & 0xffu);
+      start = (i == 0) || ((kb[i - 1] & 0xffu) != (unsigned)g);
+    }
+    unsigned b = __ballot_sync(kFull, start);
+    if (start) {
+      int q = base + __popc(b & lanemask_lt());
+      A.lev[q] = (uint8_t)g;
+      A.lut[g] = (uint8_t)q;
+      A.st[q] = (uint16_t)i;
+    }
+    base += __popc(b);
+  }
+  const int m = base;
+  if (lane == 0) A.st[m] = (uint16_t)N;
+  s1 = (int)redux_u32((unsigned)s1);
+  s2 = warp_sum_u64(s2);
+  __syncwarp();
+  // level counts: entropy, uniformity
+  float ent = 0.f;
+  unsigned u2 = 0;
+  for (int q = lane; q < m; q += 32) {
+    int c = (int)A.st[q + 1] - (int)A.st[q];
+    ent += ent_term(c, N);
+    u2 += (unsigned)(c * c);
+    if (dbg_hist) dbg_hist[A.lev[q] - 1] = c;
+  }
+  u2 = redux_u32(u2);
+  // exact percentiles: (N-1)*q = 100*k + rem, P_q = (100 x_k + rem (x_k+1 - x_k)) / 100
+  long long num[5];
+  const int qs[5] = {10, 25, 50, 75, 90};
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    int hq = (N - 1) * qs[t];
+    int k = hq / 100, rem = hq % 100;
+    long long xk = xs(k);
+    num[t] = 100 * xk + (rem ? (long long)rem * (xs(k + 1) - xk) : 0);
+  }
+  // pass 2: central moments from d = N x - S1 (exact), robust-range counts
+  __int128 d2 = 0, d3 = 0, d4 = 0;
+  unsigned long long dabs = 0;
+  unsigned below10 = 0, upto90 = 0;
+  for (int i = lane; i < N; i += 32) {
+    const long long x = xs(i);
+    const long long d = (long long)N * x - s1;
+    const long long dd = d * d;
+    d2 += (__int128)dd;
+    d3 += (__int128)dd * d;
+    d4 += (__int128)dd * dd;
+    dabs += (unsigned long long)(d < 0 ? -d : d);
+    below10 += (100 * x < num[0]);
+    upto90 += (100 * x <= num[4]);
+  }
+  d2 = warp_sum_i128(d2);
+  d3 = warp_sum_i128(d3);
+  d4 = warp_sum_i128(d4);
+  dabs = warp_sum_u64(dabs);
+  below10 = redux_u32(below10);
+  upto90 = redux_u32(upto90);
+  // pass 3: robust subset [below10, upto90)
+  const int rn = (int)upto90 - (int)below10;
+  int rs = 0;
+  for (int i = (int)below10 + lane; i < (int)upto90; i += 32) rs += xs(i);
+  rs = (int)redux_u32((unsigned)rs);
+  unsigned long long rabs = 0;
+  for (int i = (int)below10 + lane; i < (int)upto90; i += 32) {
+    long long d = (long long)rn * xs(i) - rs;
+    rabs += (unsigned long long)(d < 0 ? -d : d);
+  }
+  rabs = warp_sum_u64(rabs);
+  {
+    float e1[1] = {ent};
+    warp_sum_f32x<1>(e1);
+    ent = e1[0];
+  }
+  if (lane == 0) {
+    const float fn = (float)N;
+    const float m2 = i128_to_f32(d2);  // = N^3 * variance
+    float* f = A.fv;
+    f[0] = (float)s2;
+    f[1] = (float)job.voxel_volume * (float)s2;
+    f[2] = ent;
+    f[3] = (float)xs(0);
+    f[4] = (float)num[0] / 100.f;
+    f[5] = (float)num[4] / 100.f;
+    f[6] = (float)xs(N - 1);
+    f[7] = (float)s1 / fn;
+    f[8] = (float)num[2] / 100.f;
+    f[9] = (float)(num[3] - num[1]) / 100.f;
+    f[10] = (float)(xs(N - 1) - xs(0));
+    f[11] = (float)dabs / (fn * fn);
+    f[12] = rn > 0 ? (float)rabs / ((float)rn * (float)rn) : kNaNf;
+    f[13] = sqrtf((float)s2 / fn);
+    if (m2 == 0.f) {
+      f[14] = kNaNf;
+      f[15] = kNaNf;
+    } else {
+      f[14] = i128_to_f32(d3) * sqrtf(fn) / (m2 * sqrtf(m2));
+      f[15] = fn * (i128_to_f32(d4) / m2) / m2 - (job.kurt_excess ? 3.f : 0.f);
+    }
+    f[16] = m2 / (fn * fn * fn);
+    f[17] = (float)u2 / (fn * fn);
+  }
+  w.m = m;
+  w.lev0 = A.lev[0];
+  w.R = (int)A.lev[m - 1] - (int)A.lev[0];
+  w.u2 = u2;
+  __syncwarp();
+}
+
+// lvl[p]: level -> compact index + 1 (0 stays 0)
+__device__ void compact_levels(const Win& w, const Arena& A) {
+  for (int p = lane_id(); p < w.W; p += 32) {
+    int g = A.lvl[p];
+    if (g) A.lvl[p] = (uint8_t)(A.lut[g] + 1);
+  }
+  __syncwarp();
+}
+
+// Per-direction accumulation: lane f < nf adds finite v into facc[f].
+__device__ __forceinline__ void acc_reset(const Arena& A) {
+  const int lane = lane_id();
+  A.facc[lane] = 0.f;
+  A.nacc[lane] = 0;
+  __syncwarp();
+}
+__device__ __forceinline__ void acc_lane(const Arena& A, int nf, float v) {
+  const int lane = lane_id();
+  if (lane < nf && !isnan(v)) {
+    A.facc[lane] += v;
+    A.nacc[lane] += 1;
+  }
+}
+__device__ __forceinline__ void acc_store(const Arena& A, int nf, int f0) {
+  __syncwarp();
+  const int lane = lane_id();
+  if (lane < nf) A.fv[f0 + lane] = A.nacc[lane] ? A.facc[lane] / (float)A.nacc[lane] : kNaNf;
+  __syncwarp();
+}
+
+// ------------------------------------------------------------------ MCC
+__device__ __forceinline__ float warp_max_pos_f32(float v) {
+  // v >= 0: the ordering of nonnegative floats matches their bit patterns
+  return __int_as_float(__reduce_max_sync(kFull, __float_as_int(v)));
+}
+
+__device__ __forceinline__ int sturm_below(const float* dd, const float* ee, int n,
+                                           float t) {
+  int c = 0;
+  float q = dd[0] - t;
+  if (q < 0.f) ++c;
+  for (int i = 1; i < n; ++i) {
+    if (fabsf(q) < 1e-30f) q = -1e-30f;
+    q = dd[i] - t - ee[i - 1] * ee[i - 1] / q;
+    if (q < 0.f) ++c;
+  }
+  return c;
+}
+
+// Largest |eigenvalue| of the symmetric n x n matrix A (stride mc, fp32):
+// Householder tridiagonalisation (warp-cooperative, A overwritten), then
+// Sturm-sequence multisection over 32 shifts per round.  Used for
+// directions with more than kCapL present levels.
+__device__ float spectral_radius(float* A, int n, int mc, float* vv, float* ww,
+                                 float* dd, float* ee) {
+  const int lane = lane_id();
+  for (int k = 0; k + 2 < n; ++k) {
+    float tail = 0.f;
+    for (int i = k + 2 + lane; i < n; i += 32) {
+      float x = A[i * mc + k];
+      tail += x * x;
+    }
+    {
+      float t1[1] = {tail};
+      warp_sum_f32x<1>(t1);
+      tail = t1[0];
+    }
+    const float x1 = A[(k + 1) * mc + k];
+    if (tail == 0.f) {
+      if (lane == 0) {
+        dd[k] = A[k * mc + k];
+        ee[k] = x1;
+      }
+      continue;
+    }
+    const float alpha = -copysignf(sqrtf(tail + x1 * x1), x1);
+    const float inv = 1.0f / sqrtf(2.f * (alpha * alpha - alpha * x1));
+    for (int i = k + 1 + lane; i < n; i += 32)
+      vv[i] = (i == k + 1 ? x1 - alpha : A[i * mc + k]) * inv;
+    __syncwarp();
+    float kp = 0.f;
+    for (int i = k + 1 + lane; i < n; i += 32) {
+      float acc = 0.f;
+      for (int j = k + 1; j < n; ++j) acc += A[i * mc + j] * vv[j];
+      ww[i] = acc;
+      kp += vv[i] * acc;
+    }
+    {
+      float t1[1] = {kp};
+      warp_sum_f32x<1>(t1);
+      kp = t1[0];
+    }
+    for (int i = k + 1 + lane; i < n; i += 32) ww[i] -= kp * vv[i];
+    __syncwarp();
+    for (int i = k + 1 + lane; i < n; i += 32) {
+      const float vi = vv[i], wi = ww[i];
+      for (int j = k + 1; j < n; ++j) A[i * mc + j] -= 2.f * (vi * ww[j] + wi * vv[j]);
+    }
+    if (lane == 0) {
+      dd[k] = A[k * mc + k];
+      ee[k] = alpha;
+    }
+    __syncwarp();
+  }
+  __syncwarp();
+  if (lane == 0) {
+    if (n >= 2) {
+      dd[n - 2] = A[(n - 2) * mc + (n - 2)];
+      ee[n - 2] = A[(n - 1) * mc + (n - 2)];
+    }
+    dd[n - 1] = A[(n - 1) * mc + (n - 1)];
+  }
+  __syncwarp();
+  float bnd = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    float r = fabsf(dd[i]);
+    if (i > 0) r += fabsf(ee[i - 1]);
+    if (i < n - 1) r += fabsf(ee[i]);
+    bnd = fmaxf(bnd, r);
+  }
+  bnd = warp_max_pos_f32(bnd);
+  float lo = 0.f, hi = bnd * 1.0001f + 1e-20f;
+  for (int round = 0; round < 6; ++round) {
+    const float step = (hi - lo) / 33.f;
+    const float sig = lo + step * (float)(lane + 1);
+    const int cnt = (n - sturm_below(dd, ee, n, sig)) + sturm_below(dd, ee, n, -sig);
+    const unsigned msk = __ballot_sync(kFull, cnt > 0);
+    if (msk == 0u) {
+      hi = lo + step;
+    } else {
+      const int L = 31 - __clz(msk);
+      const float nlo = lo + step * (float)(L + 1);
+      const float nhi = (L == 31) ? hi : lo + step * (float)(L + 2);
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  return 0.5f * (lo + hi);
+}
+
+// Number of eigenvalues below t of the tridiagonal (d, e2 = squared
+// off-diagonal), by the signs of the LDL^T pivots.
+__device__ __forceinline__ int sturm_count(const float* d, const float* e2, int n, float t) {
+  int c = 0;
+  float q = d[0] - t;
+  c += q < 0.f;
+  for (int i = 1; i < n; ++i) {
+    if (fabsf(q) < 1e-30f) q = -1e-30f;
+    q = d[i] - t - __fdividef(e2[i - 1], q);
+    c += q < 0.f;
+  }
+  return c;
+}
+
+// Largest |eigenvalue| of a symmetric n x n matrix (2 <= n <= kCapL) held as
+// a packed upper triangle P (row i holds columns i..n-1), by one thread:
+// Householder tridiagonalisation in place, then bisection of the largest
+// and the smallest eigenvalue with Sturm counts.  sc: 3 kCapL floats.
+__device__ float serial_rho(float* P, int n, float* sc) {
+  float* w = sc;
+  float* d = sc + kCapL;
+  float* e2 = sc + 2 * kCapL;
+  auto at = [&](int i, int j) -> float& { return P[i * n - ((i * (i - 1)) >> 1) + (j - i)]; };
+  auto sym = [&](int i, int j) -> float { return i <= j ? at(i, j) : at(j, i); };
+  for (int k = 0; k + 2 < n; ++k) {
+    const float x1 = at(k, k + 1);
+    float tail = 0.f;
+    for (int i = k + 2; i < n; ++i) {
+      const float x = at(k, i);
+      tail += x * x;
+    }
+    if (tail == 0.f) {
+      d[k] = at(k, k);
+      e2[k] = x1 * x1;
+      continue;
+    }
+    const float alpha = -copysignf(sqrtf(tail + x1 * x1), x1);
+    const float inv = rsqrtf(2.f * (alpha * alpha - alpha * x1));
+    // v (unit) in row k beyond the diagonal
+    at(k, k + 1) = (x1 - alpha) * inv;
+    for (int i = k + 2; i < n; ++i) at(k, i) *= inv;
+    float K = 0.f;
+    for (int i = k + 1; i < n; ++i) {
+      float acc = 0.f;
+      for (int j = k + 1; j < n; ++j) acc += sym(i, j) * at(k, j);
+      w[i] = acc;
+      K += at(k, i) * acc;
+    }
+    for (int i = k + 1; i < n; ++i) w[i] -= K * at(k, i);
+    for (int i = k + 1; i < n; ++i) {
+      const float vi = at(k, i), wi = w[i];
+      for (int j = i; j < n; ++j) at(i, j) -= 2.f * (vi * w[j] + wi * at(k, j));
+    }
+    d[k] = at(k, k);
+    e2[k] = alpha * alpha;
+  }
+  if (n >= 2) {
+    d[n - 2] = at(n - 2, n - 2);
+    const float e = at(n - 2, n - 1);
+    e2[n - 2] = e * e;
+  }
+  d[n - 1] = at(n - 1, n - 1);
+  float bnd = 0.f, dmax = d[0], dmin = d[0];
+  for (int i = 0; i < n; ++i) {
+    float r = fabsf(d[i]);
+    if (i > 0) r += sqrtf(e2[i - 1]);
+    if (i < n - 1) r += sqrtf(e2[i]);
+    bnd = fmaxf(bnd, r);
+    dmax = fmaxf(dmax, d[i]);
+    dmin = fminf(dmin, d[i]);
+  }
+  bnd = bnd * 1.0001f + 1e-20f;
+  // largest eigenvalue in [max d_i, bnd] (interlacing), smallest in [-bnd, min d_i]
+  float lo = dmax, hi = bnd;
+  for (int it = 0; it < 24; ++it) {
+    const float mid = 0.5f * (lo + hi);
+    if (sturm_count(d, e2, n, mid) == n)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  const float lmax = 0.5f * (lo + hi);
+  lo = -bnd;
+  hi = dmin;
+  for (int it = 0; it < 24; ++it) {
+    const float mid = 0.5f * (lo + hi);
+    if (sturm_count(d, e2, n, mid) >= 1)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  const float lmin = 0.5f * (lo + hi);
+  return fmaxf(fabsf(lmax), fabsf(lmin));
+}
+
+// ------------------------------------------------------------------ GLCM
+__device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
+                            int32_t* dbg_glcm) {
+  const int lane = lane_id();
+  const int m = w.m, mc = A.mc;
+  int* cnt = (int*)(A.big + A.L.cnt);
+  int* marg = (int*)(A.big + A.L.marg);
+  int* plist = (int*)(A.big + A.L.prank);
+  int* sbin = (int*)(A.big + A.L.sbin);
+  int* dbin = (int*)(A.big + A.L.dbin);
+  float* vv = (float*)(A.big + A.L.vec);
+  float* ww = vv + mc;
+  float* dd = ww + mc;
+  float* ee = dd + mc;
+  int* mn = (int*)(A.big + A.L.mn);
+  float* mres = (float*)(A.big + A.L.mres);
+  float* slots = (float*)(A.big + A.L.slots);
+  const bool want_mcc = (job.families & kFamMCC) != 0;
+  const float ngf = (float)w.ng;
+  Magic mm;
+  mm.init((unsigned)m);
+  const int mm2 = m * m;
+  acc_reset(A);
+  for (int di = 0; di < kNumDirs; ++di) {
+    const int ddz = c_dirs[di][0] * job.delta, ddy = c_dirs[di][1] * job.delta,
+              ddx = c_dirs[di][2] * job.delta;
+    const int off = ddz * w.s2 + ddy * w.s + ddx;
+    // pairs -> upper-triangle counts over compact indices (equal keys merged)
+    int np = 0;
+    for (int base = 0; base < w.W; base += 32) {
+      const int p = base + lane;
+      int key = -1;
+      if (p < w.W) {
+        const int a = A.lvl[p];
+        if (a) {
+          int z, y, x;
+          pos_to_zyx(w, p, z, y, x);
+          if (in_cube(w, z + ddz, y + ddy, x + ddx)) {
+            const int b = A.lvl[p + off];
+            if (b) key = (min(a, b) - 1) * mc + (max(a, b) - 1);
+          }
+        }
+      }
+      const unsigned act = __ballot_sync(kFull, key >= 0);
+      if (key >= 0) {
+        const unsigned grp = __match_any_sync(act, key);
+        if ((grp & lanemask_lt()) == 0) atomicAdd(&cnt[key], __popc(grp));
+      }
+      np += __popc(act);
+    }
+    __syncwarp();
+    if (np == 0) {
+      if (lane == 0) {
+        mn[di] = 0;
+        mres[di] = kNaNf;
+      }
+      acc_lane(A, 23, kNaNf);
+      continue;
+    }
+    const int T = 2 * np;
+    const float fT = (float)T;
+    // marginals (lane a sums row a of the symmetric matrix) and present list
+    unsigned m1 = 0, m2 = 0;
+    float hx = 0.f;
+    int present = 0;
+    for (int a0 = 0; a0 < m; a0 += 32) {
+      const int a = a0 + lane;
+      int c = 0;
+      if (a < m) {
+        for (int b = 0; b < m; ++b)
+          c += b > a ? cnt[a * mc + b] : (b == a ? 2 * cnt[a * mc + a] : cnt[b * mc + a]);
+        marg[a] = c;
+        if (c) {
+          const unsigned i = A.lev[a];
+          m1 += i * (unsigned)c;
+          m2 += i * i * (unsigned)c;
+          hx += ent_term(c, T);
+        }
+      }
+      const unsigned pb = __ballot_sync(kFull, c > 0);
+      if (c > 0) plist[present + __popc(pb & lanemask_lt())] = a;
+      present += __popc(pb);
+    }
+    m1 = redux_u32(m1);
+    m2 = redux_u32(m2);
+    __syncwarp();
+    // entries: linear sums, entropies, mutual information, sum / difference bins
+    unsigned a1 = 0, e2 = 0, maxc = 0;
+    float hxy = 0.f, mi = 0.f;
+    for (int t0 = 0; t0 < mm2; t0 += 32) {
+      const int t = t0 + lane;
+      if (t >= mm2) continue;
+      const int a = (int)mm.div((unsigned)t), b = t - a * m;
+      if (b < a) continue;
+      const int n = cnt[a * mc + b];
+      if (!n) continue;
+      const unsigned i = A.lev[a], j = A.lev[b];
+      const int C = (a == b) ? 2 * n : n;
+      const unsigned mult = (a == b) ? 1u : 2u;
+      a1 += mult * (unsigned)C * i * j;
+      e2 += mult * (unsigned)(C * C);
+      maxc = max(maxc, (unsigned)C);
+      const float fm = (float)mult;
+      hxy += fm * ent_term(C, T);
+      const int ca = marg[a], cb = marg[b];
+      mi += fm * __fdividef((float)C, fT) *
+            log2f(__fdividef((float)((long long)C * T), (float)((long long)ca * cb)));
+      atomicAdd(&sbin[i + j - 2 * w.lev0], 2 * n);
+      atomicAdd(&dbin[j - i], 2 * n);
+      if (dbg_glcm) {
+        int32_t* g = dbg_glcm + (size_t)di * w.ng * w.ng;
+        g[(i - 1) * w.ng + (j - 1)] = C;
+        g[(j - 1) * w.ng + (i - 1)] = C;
+      }
+    }
+    a1 = redux_u32(a1);
+    e2 = redux_u32(e2);
+    maxc = __reduce_max_sync(kFull, maxc);
+    __syncwarp();
+    // MCC: the deflated A = S - u u^T, S = D^-1/2 P D^-1/2 over present levels
+    if (want_mcc) {
+      const int nd = present;
+      if (nd < 2) {
+        if (lane == 0) {
+          mn[di] = 0;
+          mres[di] = kNaNf;
+        }
+      } else if (nd <= kCapL) {
+        // packed slot: A(a', b') = (C T - c_a c_b) / (T sqrt(c_a c_b))
+        float* P = slots + di * kSlot;
+        const int nn = nd * nd;
+        for (int t = lane; t < nn; t += 32) {
+          const int ap = t / nd, bp = t - ap * nd;
+          if (bp < ap) continue;
+          const int a = plist[ap], b = plist[bp];
+          const int n = cnt[min(a, b) * mc + max(a, b)];
+          const int C = (a == b) ? 2 * n : n;
+          const int ca = marg[a], cb = marg[b];
+          const long long num = (long long)C * T - (long long)ca * cb;
+          P[ap * nd - ((ap * (ap - 1)) >> 1) + (bp - ap)] =
+              (float)num * rsqrtf((float)ca * (float)cb) / fT;
+        }
+        if (lane == 0) mn[di] = nd;
+      } else {
+        // many levels: warp-cooperative solve now, on S in place of the counts
+        float* S = (float*)cnt;
+        for (int t = lane; t < mm2; t += 32) {
+          const int a = (int)mm.div((unsigned)t), b = t - a * m;
+          if (b < a) continue;
+          const int n = cnt[a * mc + b];
+          const int ca = marg[a], cb = marg[b];
+          float v = 0.f;
+          if (ca && cb) {
+            const int C = (a == b) ? 2 * n : n;
+            const long long num = (long long)C * T - (long long)ca * cb;
+            v = (float)num * rsqrtf((float)ca * (float)cb) / fT;
+          }
+          S[a * mc + b] = v;
+          S[b * mc + a] = v;
+        }
+        __syncwarp();
+        const float rho = spectral_radius(S, m, mc, vv, ww, dd, ee);
+        if (lane == 0) {
+          mn[di] = 0;
+          mres[di] = rho;
+        }
+      }
+    }
+    __syncwarp();
+    for (int t = lane; t < mm2; t += 32) {
+      const int a = (int)mm.div((unsigned)t);
+      cnt[a * mc + (t - a * m)] = 0;
+    }
+    for (int a = lane; a < m; a += 32) {
+      marg[a] = 0;
+      plist[a] = 0;
+    }
+    // difference and sum distributions (bins relative to the smallest level)
+    unsigned dk = 0, dk2 = 0, sk = 0;
+    float de = 0.f, idm = 0.f, idmn = 0.f, idd = 0.f, idn = 0.f, iv = 0.f, se = 0.f,
+          ce2 = 0.f, ce4 = 0.f;
+    __int128 ce3 = 0;
+    const int nb = 2 * w.R + 1;
+    for (int k = lane; k < nb; k += 32) {
+      if (k <= w.R) {
+        const int c = dbin[k];
+        if (c) {
+          dbin[k] = 0;
+          const float fk = (float)k, fc = (float)c;
+          dk += (unsigned)(k * c);
+          dk2 += (unsigned)(k * k * c);
+          de += ent_term(c, T);
+          idm += __fdividef(fc, 1.f + fk * fk);
+          idmn += __fdividef(fc, 1.f + __fdividef(fk * fk, ngf * ngf));
+          idd += __fdividef(fc, 1.f + fk);
+          idn += __fdividef(fc, 1.f + __fdividef(fk, ngf));
+          if (k) iv += __fdividef(fc, fk * fk);
+        }
+      }
+      const int c = sbin[k];
+      if (c) {
+        sbin[k] = 0;
+        const int kk = k + 2 * w.lev0;
+        sk += (unsigned)(kk * c);
+        se += ent_term(c, T);
+        const int e = T * kk - 2 * (int)m1;  // T (k - 2 mu), |e| < 2^24
+        const float fe = (float)e, fe2 = fe * fe;
+        ce2 += (float)c * fe2;
+        ce4 += (float)c * fe2 * fe2;
+        ce3 += (__int128)((long long)e * e * c) * e;
+      }
+    }
+    dk = redux_u32(dk);
+    dk2 = redux_u32(dk2);
+    sk = redux_u32(sk);
+    ce3 = warp_sum_i128(ce3);
+    float fs[12] = {hx, hxy, mi, de, idm, idmn, idd, idn, iv, se, ce2, ce4};
+    warp_sum_f32x<12>(fs);
+    // one lane per feature
+    float num = kNaNf, den = 1.f;
+    const long long var_num = (long long)T * m2 - (long long)m1 * m1;  // T^2 sigma^2
+    switch (lane) {
+      case 0: num = (float)a1; den = fT; break;
+      case 1: num = (float)m1; den = fT; break;
+      case 2: num = fs[11]; den = fT * fT * fT * fT * fT; break;
+      case 3: num = i128_to_f32(ce3); den = fT * fT * fT * fT; break;
+      case 4: num = fs[10]; den = fT * fT * fT; break;
+      case 5: num = (float)dk2; den = fT; break;
+      case 6: num = (float)((long long)T * a1 - (long long)m1 * m1); den = (float)var_num; break;
+      case 7: num = (float)dk; den = fT; break;
+      case 8: num = fs[3]; break;
+      case 9: num = (float)((long long)T * dk2 - (long long)dk * dk); den = fT * fT; break;
+      case 10: num = (float)e2; den = fT * fT; break;
+      case 11: num = fs[1]; break;
+      case 12: num = -fs[2]; den = fs[0]; break;
+      case 13: num = sqrtf(fmaxf(0.f, -expm1f(-2.f * fs[2]))); break;
+      case 14: num = fs[4]; den = fT; break;
+      case 15: num = fs[5]; den = fT; break;
+      case 16: num = fs[6]; den = fT; break;
+      case 17: num = fs[7]; den = fT; break;
+      case 18: num = fs[8]; den = fT; break;
+      case 19: num = (float)maxc; den = fT; break;
+      case 20: num = (float)sk; den = fT; break;
+      case 21: num = fs[9]; break;
+      case 22: num = (float)var_num; den = fT * fT; break;
+      default: break;
+    }
+    acc_lane(A, 23, lane_quot(num, den));
+  }
+  __syncwarp();
+  if (want_mcc) {
+    if (lane < kNumDirs && mn[lane] >= 2) {
+      const int n = mn[lane];
+      float* P = slots + lane * kSlot;
+      mres[lane] = serial_rho(P, n, P + kCapL * (kCapL + 1) / 2);
+    }
+    __syncwarp();
+    if (lane == 23) {
+      float s = 0.f;
+      int c = 0;
+      for (int d = 0; d < kNumDirs; ++d) {
+        const float v = mres[d];
+        if (!isnan(v)) {
+          s += v;
+          ++c;
+        }
+      }
+      A.facc[23] = s;
+      A.nacc[23] = c;
+    }
+  }
+  acc_store(A, want_mcc ? 24 : 23, 18);
+}
+
+// ------------------------------------------------------------------ GLRLM
+__device__ void glrlm_family(const Win& w, const Arena& A, int32_t* dbg_glrlm) {
+  const int lane = lane_id();
+  const int m = w.m;
+  int* hist = (int*)(A.big + A.L.rhist);  // [mc][16]
+  int* lnc = (int*)(A.big + A.L.rlen);    // column sums when m > 32
+  acc_reset(A);
+  const float nvf = (float)w.nv;
+  for (int di = 0; di < kNumDirs; ++di) {
+    const int dz = c_dirs[di][0], dy = c_dirs[di][1], dx = c_dirs[di][2];
+    const int off = dz * w.s2 + dy * w.s + dx;
+    int nr = 0;
+    for (int base = 0; base < w.W; base += 32) {
+      const int p = base + lane;
+      int key = -1;
+      if (p < w.W) {
+        const int a = A.lvl[p];
+        if (a) {
+          int z, y, x;
+          pos_to_zyx(w, p, z, y, x);
+          if (!(in_cube(w, z - dz, y - dy, x - dx) && A.lvl[p - off] == a)) {
+            int len = 1, q = p + off, zz = z + dz, yy = y + dy, xx = x + dx;
+            while (in_cube(w, zz, yy, xx) && A.lvl[q] == a) {
+              ++len;
+              q += off;
+              zz += dz;
+              yy += dy;
+              xx += dx;
+            }
+            key = (a - 1) * 16 + (len - 1);
+          }
+        }
+      }
+      const unsigned act = __ballot_sync(kFull, key >= 0);
+      if (key >= 0) {
+        const unsigned grp = __match_any_sync(act, key);
+        if ((grp & lanemask_lt()) == 0) atomicAdd(&hist[key], __popc(grp));
+      }
+      nr += __popc(act);
+    }
+    __syncwarp();
+    // row walk: lane a owns gray level a; columns are run lengths
+    unsigned si = 0, si2 = 0, sj = 0, sj2 = 0, glnu = 0, rlnu = 0;
+    float fs[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sre lgl srl srh lrl lrh ent
+    for (int a0 = 0; a0 < m; a0 += 32) {
+      const int a = a0 + lane;
+      const bool ok = a < m;
+      const unsigned i = ok ? A.lev[a] : 1u;
+      const float fi2 = (float)(i * i), inv_i2 = __fdividef(1.f, fi2);
+      unsigned row = 0;
+      for (int jl = 0; jl < w.s; ++jl) {
+        const int c = ok ? hist[a * 16 + jl] : 0;
+        const unsigned col = redux_u32((unsigned)c);
+        if (m <= 32)
+          rlnu += col * col;
+        else if (lane == 0)
+          lnc[jl] += (int)col;
+        if (c) {
+          hist[a * 16 + jl] = 0;
+          const unsigned J = (unsigned)(jl + 1);
+          const float fc = (float)c, fj2 = (float)(J * J), inv_j2 = __fdividef(1.f, fj2);
+          row += (unsigned)c;
+          si += (unsigned)c * i;
+          si2 += (unsigned)c * i * i;
+          sj += (unsigned)c * J;
+          sj2 += (unsigned)c * J * J;
+          fs[0] += fc * inv_j2;
+          fs[1] += fc * inv_i2;
+          fs[2] += fc * inv_i2 * inv_j2;
+          fs[3] += fc * fi2 * inv_j2;
+          fs[4] += fc * fj2 * inv_i2;
+          fs[5] += fc * fi2 * fj2;
+          fs[6] += ent_term(c, nr);
+          if (dbg_glrlm) dbg_glrlm[((size_t)di * w.ng + (i - 1)) * w.s + jl] = c;
+        }
+      }
+      glnu += row * row;
+    }
+    if (m > 32) {
+      __syncwarp();
+      if (lane < 16) {
+        const unsigned c = (unsigned)lnc[lane];
+        lnc[lane] = 0;
+        rlnu = c * c;
+      }
+      rlnu = redux_u32(rlnu);
+    }
+    si = redux_u32(si);
+    si2 = redux_u32(si2);
+    sj = redux_u32(sj);
+    sj2 = redux_u32(sj2);
+    glnu = redux_u32(glnu);
+    warp_sum_f32x<7>(fs);
+    const float N = (float)nr;
+    float num = kNaNf, den = N;
+    switch (lane) {
+      case 0: num = fs[0]; break;
+      case 1: num = (float)sj2; break;
+      case 2: num = (float)glnu; break;
+      case 3: num = (float)glnu; den = N * N; break;
+      case 4: num = (float)rlnu; break;
+      case 5: num = (float)rlnu; den = N * N; break;
+      case 6: num = N; den = nvf; break;
+      case 7: num = (float)((long long)nr * si2 - (long long)si * si); den = N * N; break;
+      case 8: num = (float)((long long)nr * sj2 - (long long)sj * sj); den = N * N; break;
+      case 9: num = fs[6]; den = 1.f; break;
+      case 10: num = fs[1]; break;
+      case 11: num = (float)si2; break;
+      case 12: num = fs[2]; break;
+      case 13: num = fs[3]; break;
+      case 14: num = fs[4]; break;
+      case 15: num = fs[5]; break;
+      default: break;
+    }
+    acc_lane(A, 16, lane_quot(num, den));
+  }
+  acc_store(A, 16, 42);
+}
+
+// ------------------------------------------------------------------ GLSZM
+__device__ __forceinline__ int uf_find(volatile int* parent, int x) {
+  int cur = parent[x];
+  if (cur != x) {
+    int prev = x, next;
+    while (cur > (next = parent[cur])) {
+      parent[prev] = next;  // path halving; only ever points to an ancestor
+      prev = cur;
+      cur = next;
+    }
+  }
+  return cur;
+}
+
+__device__ __forceinline__ void uf_unite(int* parent, int a, int b) {
+  volatile int* vp = parent;
+  while (true) {
+    a = uf_find(vp, a);
+    b = uf_find(vp, b);
+    if (a == b) return;
+    if (a < b) {
+      int t = a;
+      a = b;
+      b = t;
+    }
+    // hook root a under the smaller root b if a is still a root
+    if (atomicCAS(&parent[a], a, b) == a) return;
+  }
+}
+
+__device__ void glszm_family(const Win& w, const Arena& A, int32_t* dbg_glszm) {
+  const int lane = lane_id();
+  const int m = w.m;
+  int* parent = (int*)(A.big + A.L.parent);
+  int* zsz = (int*)(A.big + A.L.zsz);
+  int* zlv = (int*)(A.big + A.L.zlv);
+  for (int p = lane; p < w.W; p += 32) {
+    parent[p] = p;
+    zsz[p] = 0;
+  }
+  for (int a = lane; a < m; a += 32) zlv[a] = 0;
+  __syncwarp();
+  for (int p = lane; p < w.W; p += 32) {
+    const int a = A.lvl[p];
+    if (!a) continue;
+    int z, y, x;
+    pos_to_zyx(w, p, z, y, x);
+    for (int di = 0; di < kNumDirs; ++di) {
+      const int dz = c_dirs[di][0], dy = c_dirs[di][1], dx = c_dirs[di][2];
+      if (!in_cube(w, z + dz, y + dy, x + dx)) continue;
+      const int q = p + dz * w.s2 + dy * w.s + dx;
+      if (A.lvl[q] == a) uf_unite(parent, p, q);
+    }
+  }
+  __syncwarp();
+  for (int p = lane; p < w.W; p += 32) {
+    if (!A.lvl[p]) continue;
+    atomicAdd(&zsz[uf_find((volatile int*)parent, p)], 1);
+  }
+  __syncwarp();
+  // zones: roots of V(v) components -> keys (size << 8 | compact level)
+  int nz = 0;
+  unsigned si = 0, si2 = 0, sj2 = 0;
+  float fs[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sae lgl sal sah lal lah ze
+  for (int base = 0; base < w.W; base += 32) {
+    const int p = base + lane;
+    bool root = false;
+    int a = 0, size = 0;
+    if (p < w.W) {
+      a = A.lvl[p];
+      root = a && parent[p] == p;
+      if (root) size = zsz[p];
+    }
+    const unsigned b = __ballot_sync(kFull, root);
+    if (root) {
+      A.kb[nz + __popc(b & lanemask_lt())] = ((uint32_t)size << 8) | (uint32_t)(a - 1);
+      const unsigned i = A.lev[a - 1];
+      const unsigned j = (unsigned)size;
+      si += i;
+      si2 += i * i;
+      sj2 += j * j;
+      const float fi2 = (float)(i * i), fj2 = (float)(j * j);
+      const float inv_i2 = __fdividef(1.f, fi2), inv_j2 = __fdividef(1.f, fj2);
+      fs[0] += inv_j2;
+      fs[1] += inv_i2;
+      fs[2] += inv_i2 * inv_j2;
+      fs[3] += fi2 * inv_j2;
+      fs[4] += fj2 * inv_i2;
+      fs[5] += fi2 * fj2;
+      atomicAdd(&zlv[a - 1], 1);
+      if (dbg_glszm) atomicAdd(&dbg_glszm[(size_t)(i - 1) * w.W + (j - 1)], 1);
+    }
+    nz += __popc(b);
+  }
+  __syncwarp();
+  warp_sort(A.kb, nz);
+  unsigned sznu = 0, glnu = 0;
+  for (int i = lane; i < nz; i += 32) {
+    const uint32_t key = A.kb[i];
+    if (i == 0 || A.kb[i - 1] != key) {
+      const int c = lower_bound_u32(A.kb, i, nz, key + 1) - i;
+      fs[6] += ent_term(c, nz);
+    }
+    if (i == 0 || (A.kb[i - 1] >> 8) != (key >> 8)) {
+      const unsigned c = (unsigned)(lower_bound_u32(A.kb, i, nz, ((key >> 8) + 1) << 8) - i);
+      sznu += c * c;
+    }
+  }
+  for (int a = lane; a < m; a += 32) {
+    const unsigned c = (unsigned)zlv[a];
+    zlv[a] = 0;
+    glnu += c * c;
+  }
+  si = redux_u32(si);
+  si2 = redux_u32(si2);
+  sj2 = redux_u32(sj2);
+  sznu = redux_u32(sznu);
+  glnu = redux_u32(glnu);
+  warp_sum_f32x<7>(fs);
+  // the big region is shared by the families, which count into it from zero
+  for (int p = lane; p < w.W; p += 32) {
+    parent[p] = 0;
+    zsz[p] = 0;
+  }
+  const float N = (float)nz;
+  const unsigned sj = (unsigned)w.nv;  // zone sizes add up to N_v
+  float num = kNaNf, den = N;
+  switch (lane) {
+    case 0: num = fs[0]; break;
+    case 1: num = (float)sj2; break;
+    case 2: num = (float)glnu; break;
+    case 3: num = (float)glnu; den = N * N; break;
+    case 4: num = (float)sznu; break;
+    case 5: num = (float)sznu; den = N * N; break;
+    case 6: num = N; den = (float)w.nv; break;
+    case 7: num = (float)((long long)nz * si2 - (long long)si * si); den = N * N; break;
+    case 8: num = (float)((long long)nz * sj2 - (long long)sj * sj); den = N * N; break;
+    case 9: num = fs[6]; den = 1.f; break;
+    case 10: num = fs[1]; break;
+    case 11: num = (float)si2; break;
+    case 12: num = fs[2]; break;
+    case 13: num = fs[3]; break;
+    case 14: num = fs[4]; break;
+    case 15: num = fs[5]; break;
+    default: break;
+  }
+  if (lane < 16) A.fv[58 + lane] = lane_quot(num, den);
+  __syncwarp();
+}
+
+// ------------------------------------------------------------------ GLDM + NGTDM
+__device__ void gldm_ngtdm_family(const Win& w, const Arena& A, const FrJob& job,
+                                  int32_t* dbg_gldm, int32_t* dbg_ngn,
+                                  long long* dbg_ngs) {
+  const int lane = lane_id();
+  const int m = w.m;
+  const bool do_gldm = (job.families & kFamGLDM) != 0;
+  const bool do_ngtdm = (job.families & kFamNGTDM) != 0;
+  int* gh = (int*)(A.big + A.L.ghist);  // [mc][28]
+  int* gj = (int*)(A.big + A.L.gj);
+  int* ngn = (int*)(A.big + A.L.ngn);
+  unsigned long long* ngs = (unsigned long long*)(A.big + A.L.ngs);
+  for (int base = 0; base < w.W; base += 32) {
+    const int p = base + lane;
+    int key = -1;
+    if (p < w.W) {
+      const int a = A.lvl[p];
+      if (a) {
+        int z, y, x;
+        pos_to_zyx(w, p, z, y, x);
+        int keq = 0, nw = 0, ssum = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              if (!dz && !dy && !dx) continue;
+              if (!in_cube(w, z + dz, y + dy, x + dx)) continue;
+              const int b = A.lvl[p + dz * w.s2 + dy * w.s + dx];
+              if (!b) continue;
+              ++nw;
+              ssum += A.lev[b - 1];
+              keq += (b == a);
+            }
+        key = (a - 1) * 28 + keq;
+        if (do_ngtdm && nw > 0) {
+          const long long i = A.lev[a - 1];
+          long long dlt = i * nw - ssum;
+          if (dlt < 0) dlt = -dlt;
+          atomicAdd(&ngn[a - 1], 1);
+          atomicAdd(&ngs[a - 1], (unsigned long long)(dlt * c_ldiv.v[nw]));
+        }
+      }
+    }
+    if (do_gldm) {
+      const unsigned act = __ballot_sync(kFull, key >= 0);
+      if (key >= 0) {
+        const unsigned grp = __match_any_sync(act, key);
+        if ((grp & lanemask_lt()) == 0) atomicAdd(&gh[key], __popc(grp));
+      }
+    }
+  }
+  __syncwarp();
+  const int N = w.nv;
+  if (do_gldm) {
+    unsigned si = 0, si2 = 0, sj = 0, sj2 = 0, dnu = 0;
+    float fs[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sde lgl sdl sdh ldl ldh de
+    for (int a0 = 0; a0 < m; a0 += 32) {
+      const int a = a0 + lane;
+      const bool ok = a < m;
+      const unsigned i = ok ? A.lev[a] : 1u;
+      const float fi2 = (float)(i * i), inv_i2 = __fdividef(1.f, fi2);
+      for (int k = 0; k < 27; ++k) {
+        const int c = ok ? gh[a * 28 + k] : 0;
+        const unsigned col = redux_u32((unsigned)c);
+        if (m <= 32)
+          dnu += col * col;
+        else if (lane == 0)
+          gj[k] += (int)col;
+        if (c) {
+          gh[a * 28 + k] = 0;
+          const unsigned J = (unsigned)(k + 1);
+          const float fc = (float)c, fj2 = (float)(J * J), inv_j2 = __fdividef(1.f, fj2);
+          si += (unsigned)c * i;
+          si2 += (unsigned)c * i * i;
+          sj += (unsigned)c * J;
+          sj2 += (unsigned)c * J * J;
+          fs[0] += fc * inv_j2;
+          fs[1] += fc * inv_i2;
+          fs[2] += fc * inv_i2 * inv_j2;
+          fs[3] += fc * fi2 * inv_j2;
+          fs[4] += fc * fj2 * inv_i2;
+          fs[5] += fc * fi2 * fj2;
+          fs[6] += ent_term(c, N);
+          if (dbg_gldm) dbg_gldm[(i - 1) * 27 + k] = c;
+        }
+      }
+    }
+    if (m > 32) {
+      __syncwarp();
+      if (lane < 28) {
+        const unsigned c = (unsigned)gj[lane];
+        gj[lane] = 0;
+        dnu = c * c;
+      }
+      dnu = redux_u32(dnu);
+    }
+    si = redux_u32(si);
+    si2 = redux_u32(si2);
+    sj = redux_u32(sj);
+    sj2 = redux_u32(sj2);
+    warp_sum_f32x<7>(fs);
+    const float fN = (float)N;
+    float num = kNaNf, den = fN;
+    switch (lane) {
+      case 0: num = fs[0]; break;
+      case 1: num = (float)sj2; break;
+      case 2: num = (float)w.u2; break;
+      case 3: num = (float)dnu; break;
+      case 4: num = (float)dnu; den = fN * fN; break;
+      case 5: num = (float)((long long)N * si2 - (long long)si * si); den = fN * fN; break;
+      case 6: num = (float)((long long)N * sj2 - (long long)sj * sj); den = fN * fN; break;
+      case 7: num = fs[6]; den = 1.f; break;
+      case 8: num = fs[1]; break;
+      case 9: num = (float)si2; break;
+      case 10: num = fs[2]; break;
+      case 11: num = fs[3]; break;
+      case 12: num = fs[4]; break;
+      case 13: num = fs[5]; break;
+      default: break;
+    }
+    if (lane < 14) A.fv[74 + lane] = lane_quot(num, den);
+  }
+  __syncwarp();
+  if (do_ngtdm) {
+    // per-level sums over present levels, then the pairwise sums
+    const float invL = (float)(1.0 / (double)kLcm26);
+    unsigned nvp = 0, ngp = 0;
+    unsigned long long sls = 0;
+    float nsf = 0.f;
+    for (int a = lane; a < m; a += 32) {
+      const int n = ngn[a];
+      if (!n) continue;
+      const unsigned long long sl = ngs[a];
+      nvp += (unsigned)n;
+      sls += sl;
+      nsf += (float)n * ((float)sl * invL);
+      ++ngp;
+      if (dbg_ngn) {
+        dbg_ngn[A.lev[a] - 1] = n;
+        dbg_ngs[A.lev[a] - 1] = (long long)sl;
+      }
+    }
+    nvp = redux_u32(nvp);
+    ngp = redux_u32(ngp);
+    sls = warp_sum_u64(sls);
+    unsigned long long c1 = 0, bden = 0, str = 0;
+    float cpl = 0.f;
+    for (int a = lane; a < m; a += 32) {
+      const long long na = ngn[a];
+      if (!na) continue;
+      const long long ia = A.lev[a];
+      const float sa = (float)ngs[a] * invL;
+      for (int b = 0; b < m; ++b) {
+        const long long nb = ngn[b];
+        if (!nb) continue;
+        const long long ib = A.lev[b];
+        const long long d = ia - ib;
+        c1 += (unsigned long long)(na * nb * d * d);
+        const long long bd = ia * na - ib * nb;
+        bden += (unsigned long long)(bd < 0 ? -bd : bd);
+        str += (unsigned long long)((na + nb) * d * d);
+        const float sb = (float)ngs[b] * invL;
+        cpl += __fdividef((float)(d < 0 ? -d : d) * ((float)na * sa + (float)nb * sb),
+                          (float)(na + nb));
+      }
+    }
+    c1 = warp_sum_u64(c1);
+    bden = warp_sum_u64(bden);
+    str = warp_sum_u64(str);
+    float fs[2] = {nsf, cpl};
+    warp_sum_f32x<2>(fs);
+    __syncwarp();
+    for (int a = lane; a < m; a += 32) {
+      ngn[a] = 0;
+      ngs[a] = 0ull;
+    }
+    const float fv = (float)nvp, slsf = (float)sls * invL;
+    float num = kNaNf, den = 1.f;
+    if (nvp) {
+      switch (lane) {
+        case 0: num = fv; den = fs[0]; break;
+        case 1:
+          if (ngp == 1) {
+            num = 0.f;
+          } else {
+            num = (float)c1 * slsf;
+            den = fv * fv * (float)ngp * (float)(ngp - 1) * fv;
+          }
+          break;
+        case 2: num = fs[0]; den = (float)bden; break;
+        case 3: num = fs[1]; den = fv; break;
+        case 4: num = (float)str; den = fv * slsf; break;
+        default: break;
+      }
+    }
+    if (lane < 5) A.fv[88 + lane] = (nvp == 0) ? kNaNf : lane_quot(num, den);
+  }
+  __syncwarp();
+}
+
+}  // namespace fr
