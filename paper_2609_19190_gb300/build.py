@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(LIB_DIR, "libflashmap.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
-              "-Xcompiler", "-fno-strict-aliasing", "--expt-relaxed-constexpr",
+              "-Xcompiler", "-fno-strict-aliasing", "--expt-relaxed-constexpr", "-prec-sqrt=false",
               "-I" + INCLUDE, "-I" + CSRC]
 
 

@@ -163,12 +163,12 @@ bool valid_params(const fr_map_params* p) {
 
 fr_tune default_tune(const fr_tune* t) {
   fr_tune d;
-  d.brick_x = 16;
-  d.brick_y = 8;
-  d.brick_z = 8;
-  d.voxels_per_item = 64;
+  d.brick_x = 8;
+  d.brick_y = 4;
+  d.brick_z = 4;
+  d.voxels_per_item = 16;
   d.consumer_warps = 16;
-  d.stages = 2;
+  d.stages = 1;
   d.ctas_per_sm = 0;
   if (t) {
     if (t->brick_x) d.brick_x = t->brick_x;

@@ -36,84 +36,122 @@ __host__ __device__ inline CtaLayout fr_cta_layout(int stages, int tile_bytes,
   return c;
 }
 
+// Consumer warps of a CTA map their voxels of an item family by family, in
+// step: a named barrier (id 1, consumer threads only) after each family keeps
+// the warps in the same code region, so they share the instruction cache.
+__device__ __forceinline__ void consumer_bar(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// OR of a per-thread flag over the consumer threads (a barrier as well).
+__device__ __forceinline__ bool consumer_any(bool flag, int nthreads) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, %2, q;\n\t"
+      "selp.s32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"((unsigned)flag), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
+// Voxel t of the item, or no voxel (has == false: the warp only keeps step).
 template <bool DUMP>
 __device__ void map_voxel(const FrMapArgs& args, const FrJob& job,
-                          const FrItem& item, const uint32_t* tile, int col,
-                          Arena& A, char* smem_big, char* slab_big, int it) {
+                          const FrItem& item, const uint32_t* tile, int t, bool has,
+                          Arena& A, char* smem_big, char* slab_big, int it, int nt) {
   const int lane = lane_id();
-  const int lin = job.voi[col];
-  const int x = lin % job.nx;
-  const int y = (lin / job.nx) % job.ny;
-  const int z = lin / (job.nx * job.ny);
   Win w;
-  w.r = job.r;
-  w.s = 2 * job.r + 1;
-  w.s2 = w.s * w.s;
-  w.W = w.s2 * w.s;
-  w.ms.init((unsigned)w.s);
-  w.ms2.init((unsigned)w.s2);
-  w.ng = job.state->ng;
-  const int cx = (x - job.r) - (item.bx - job.hx);
-  const int cy = y - item.by;
-  const int cz = z - item.bz;
-  w.nv = gather_window(w, A, tile, job.box_x, job.box_y, cx, cy, cz);
-  warp_sort(A.kb, w.nv);
-
-  int32_t* rec = nullptr;
+  int col = 0;
+  bool skip = false;
   int32_t *d_hist = nullptr, *d_glcm = nullptr, *d_glrlm = nullptr,
           *d_glszm = nullptr, *d_gldm = nullptr, *d_ngn = nullptr;
   long long* d_ngs = nullptr;
-  if (DUMP) {
-    const int ng = w.ng;
-    rec = args.dbg + (size_t)it * args.dbg_stride;
-    d_hist = rec + 4;
-    d_glcm = d_hist + ng;
-    d_glrlm = d_glcm + (size_t)kNumDirs * ng * ng;
-    d_glszm = d_glrlm + (size_t)kNumDirs * ng * w.s;
-    d_gldm = d_glszm + (size_t)ng * w.W;
-    d_ngn = d_gldm + (size_t)ng * 27;
-    size_t o = (size_t)(d_ngn + ng - rec);
-    o = (o + 1) & ~(size_t)1;
-    d_ngs = (long long*)(rec + o);
-    if (lane == 0) {
-      rec[0] = ng;
-      rec[1] = w.s;
-      rec[2] = w.W;
-      rec[3] = w.nv;
+  if (has) {
+    col = job.bcols[item.j0 + t];
+    const int lin = job.voi[col];
+    const int x = lin % job.nx;
+    const int y = (lin / job.nx) % job.ny;
+    const int z = lin / (job.nx * job.ny);
+    w.r = job.r;
+    w.s = 2 * job.r + 1;
+    w.s2 = w.s * w.s;
+    w.W = w.s2 * w.s;
+    w.ms.init((unsigned)w.s);
+    w.ms2.init((unsigned)w.s2);
+    w.ng = job.state->ng;
+    const int cx = (x - job.r) - (item.bx - job.hx);
+    const int cy = y - item.by;
+    const int cz = z - item.bz;
+    w.nv = gather_window(w, A, tile, job.box_x, job.box_y, cx, cy, cz);
+    warp_sort(A.kb, w.nv);
+    if (DUMP) {
+      const int ng = w.ng;
+      int32_t* rec = args.dbg + (size_t)it * args.dbg_stride;
+      d_hist = rec + 4;
+      d_glcm = d_hist + ng;
+      d_glrlm = d_glcm + (size_t)kNumDirs * ng * ng;
+      d_glszm = d_glrlm + (size_t)kNumDirs * ng * w.s;
+      d_gldm = d_glszm + (size_t)ng * w.W;
+      d_ngn = d_gldm + (size_t)ng * 27;
+      size_t o = (size_t)(d_ngn + ng - rec);
+      o = (o + 1) & ~(size_t)1;
+      d_ngs = (long long*)(rec + o);
+      if (lane == 0) {
+        rec[0] = ng;
+        rec[1] = w.s;
+        rec[2] = w.W;
+        rec[3] = w.nv;
+      }
     }
-  }
-
-  first_order(w, A, job, d_hist);
-  compact_levels(w, A);
-  if (w.m > kMCap || w.R >= kBinCap) {
-    if (slab_big == nullptr) {
-      if (lane == 0) atomicCAS(args.status, 0, kStatusUnsupported);
-      for (int f = lane; f < kNumFeatures; f += 32) A.fv[f] = kNaNf;
-      __syncwarp();
-      goto store;
+    first_order(w, A, job, d_hist);
+    compact_levels(w, A);
+    if (w.m > kMCap || w.R >= kBinCap) {
+      if (slab_big == nullptr) {
+        if (lane == 0) atomicCAS(args.status, 0, kStatusUnsupported);
+        for (int f = lane; f < kNumFeatures; f += 32) A.fv[f] = kNaNf;
+        __syncwarp();
+        skip = true;
+      } else {
+        A.big = slab_big;
+        A.mc = args.slab_ngc;
+        A.bc = args.slab_ngc;
+      }
+    } else {
+      A.big = smem_big;
+      A.mc = kMCap;
+      A.bc = kBinCap;
     }
-    A.big = slab_big;
-    A.mc = args.slab_ngc;
-    A.bc = args.slab_ngc;
-  } else {
-    A.big = smem_big;
-    A.mc = kMCap;
-    A.bc = kBinCap;
+    if (!skip) A.L = fr_big_layout(A.mc, A.bc, w.W);
   }
-  A.L = fr_big_layout(A.mc, A.bc, w.W);
-  if (job.families & kFamGLCM) glcm_family(w, A, job, d_glcm);
-  if (job.families & kFamGLRLM) glrlm_family(w, A, d_glrlm);
-  if (job.families & kFamGLSZM) glszm_family(w, A, d_glszm);
-  if (job.families & (kFamGLDM | kFamNGTDM))
-    gldm_ngtdm_family(w, A, job, d_gldm, d_ngn, d_ngs);
-store:
-  __syncwarp();
-  float* out = (float*)args.run_ptrs[2 * item.job + 1];
-  for (int f = lane; f < kNumFeatures; f += 32) {
-    const int row = job.row_of[f];
-    if (row >= 0) out[(size_t)row * job.n_voi + col] = A.fv[f];
+  const bool work = has && !skip;
+  consumer_bar(nt);
+  if (job.families & kFamGLCM) {
+    if (work) glcm_family(w, A, job, d_glcm);
+    consumer_bar(nt);
   }
-  __syncwarp();
+  if (job.families & kFamGLRLM) {
+    if (work) glrlm_family(w, A, d_glrlm);
+    consumer_bar(nt);
+  }
+  if (job.families & kFamGLSZM) {
+    if (work) glszm_family(w, A, d_glszm);
+    consumer_bar(nt);
+  }
+  if (job.families & (kFamGLDM | kFamNGTDM)) {
+    if (work) gldm_ngtdm_family(w, A, job, d_gldm, d_ngn, d_ngs);
+    consumer_bar(nt);
+  }
+  if (has) {
+    float* out = (float*)args.run_ptrs[2 * item.job + 1];
+    for (int f = lane; f < kNumFeatures; f += 32) {
+      const int row = job.row_of[f];
+      if (row >= 0) out[(size_t)row * job.n_voi + col] = A.fv[f];
+    }
+    __syncwarp();
+  }
 }
 
 template <bool DUMP>
@@ -219,11 +257,15 @@ __global__ void __launch_bounds__(32 * (kMaxConsumerWarps + 1), 1)
   char* smem_big = (char*)(ab + args.arena.off_big);
   char* slab_big = args.slab ? args.slab + ((size_t)blockIdx.x * NW + warp) * args.slab_stride
                              : nullptr;
+  const int nt = 32 * NW;
   int stage = 0;
   unsigned phase = 0;
   while (true) {
-    if (!mbar_wait_bounded(&full[stage], phase, args.timeout_ns, abort_flag)) {
-      if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
+    const bool ok = mbar_wait_bounded(&full[stage], phase, args.timeout_ns, abort_flag);
+    // every consumer warp reaches this barrier; all leave together if any
+    // wait failed, so none is left waiting at a later barrier
+    if (consumer_any(!ok, nt)) {
+      if (!ok && lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
       break;
     }
     const int it = slot[stage];
@@ -231,9 +273,10 @@ __global__ void __launch_bounds__(32 * (kMaxConsumerWarps + 1), 1)
     const FrItem item = args.items[it];
     const FrJob& job = args.jobs[item.job];
     const uint32_t* tile = (const uint32_t*)(smem + cl.tiles + (size_t)stage * args.tile_bytes);
-    for (int t = warp; t < item.n; t += NW) {
-      const int col = job.bcols[item.j0 + t];
-      map_voxel<DUMP>(args, job, item, tile, col, A, smem_big, slab_big, it);
+    const int rounds = (item.n + NW - 1) / NW;
+    for (int r = 0; r < rounds; ++r) {
+      const int t = r * NW + warp;
+      map_voxel<DUMP>(args, job, item, tile, t, t < item.n, A, smem_big, slab_big, it, nt);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[stage]);

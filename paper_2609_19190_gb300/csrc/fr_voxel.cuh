@@ -145,7 +145,7 @@ __device__ __forceinline__ float i128_to_f32(__int128 v) {
 
 // One quotient per lane; a zero denominator gives NaN.
 __device__ __forceinline__ float lane_quot(float num, float den) {
-  return den == 0.f ? kNaNf : num / den;
+  return den == 0.f ? kNaNf : __fdividef(num, den);
 }
 
 // ------------------------------------------------------------------ sorting
@@ -202,8 +202,10 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t* a, int lo, int hi
   return lo;
 }
 
-// (c/n) * log2(n/c) for 0 < c <= n
+// (c/n) * log2(n/c) for 0 < c <= n; exactly 0 when c == n (a single cell
+// has zero entropy, and a zero HX is what makes Imc1 undefined)
 __device__ __forceinline__ float ent_term(int c, int n) {
+  if (c == n) return 0.f;
   const float fc = (float)c, fn = (float)n;
   return __fdividef(fc, fn) * log2f(__fdividef(fn, fc));
 }
@@ -337,25 +339,26 @@ __device__ void first_order(Win& w, const Arena& A, const FrJob& job,
     f[1] = (float)job.voxel_volume * (float)s2;
     f[2] = ent;
     f[3] = (float)xs(0);
-    f[4] = (float)num[0] / 100.f;
-    f[5] = (float)num[4] / 100.f;
+    f[4] = (float)num[0] * 0.01f;
+    f[5] = (float)num[4] * 0.01f;
     f[6] = (float)xs(N - 1);
-    f[7] = (float)s1 / fn;
-    f[8] = (float)num[2] / 100.f;
-    f[9] = (float)(num[3] - num[1]) / 100.f;
+    f[7] = __fdividef((float)s1, fn);
+    f[8] = (float)num[2] * 0.01f;
+    f[9] = (float)(num[3] - num[1]) * 0.01f;
     f[10] = (float)(xs(N - 1) - xs(0));
-    f[11] = (float)dabs / (fn * fn);
-    f[12] = rn > 0 ? (float)rabs / ((float)rn * (float)rn) : kNaNf;
-    f[13] = sqrtf((float)s2 / fn);
+    f[11] = __fdividef((float)dabs, fn * fn);
+    f[12] = rn > 0 ? __fdividef((float)rabs, (float)rn * (float)rn) : kNaNf;
+    f[13] = sqrtf(__fdividef((float)s2, fn));
     if (m2 == 0.f) {
       f[14] = kNaNf;
       f[15] = kNaNf;
     } else {
-      f[14] = i128_to_f32(d3) * sqrtf(fn) / (m2 * sqrtf(m2));
-      f[15] = fn * (i128_to_f32(d4) / m2) / m2 - (job.kurt_excess ? 3.f : 0.f);
+      f[14] = __fdividef(i128_to_f32(d3) * sqrtf(fn), m2 * sqrtf(m2));
+      f[15] = __fdividef(fn * __fdividef(i128_to_f32(d4), m2), m2) -
+              (job.kurt_excess ? 3.f : 0.f);
     }
-    f[16] = m2 / (fn * fn * fn);
-    f[17] = (float)u2 / (fn * fn);
+    f[16] = __fdividef(m2, fn * fn * fn);
+    f[17] = __fdividef((float)u2, fn * fn);
   }
   w.m = m;
   w.lev0 = A.lev[0];
@@ -390,7 +393,8 @@ __device__ __forceinline__ void acc_lane(const Arena& A, int nf, float v) {
 __device__ __forceinline__ void acc_store(const Arena& A, int nf, int f0) {
   __syncwarp();
   const int lane = lane_id();
-  if (lane < nf) A.fv[f0 + lane] = A.nacc[lane] ? A.facc[lane] / (float)A.nacc[lane] : kNaNf;
+  if (lane < nf)
+    A.fv[f0 + lane] = A.nacc[lane] ? __fdividef(A.facc[lane], (float)A.nacc[lane]) : kNaNf;
   __syncwarp();
 }
 
@@ -407,7 +411,7 @@ __device__ __forceinline__ int sturm_below(const float* dd, const float* ee, int
   if (q < 0.f) ++c;
   for (int i = 1; i < n; ++i) {
     if (fabsf(q) < 1e-30f) q = -1e-30f;
-    q = dd[i] - t - ee[i - 1] * ee[i - 1] / q;
+    q = dd[i] - t - __fdividef(ee[i - 1] * ee[i - 1], q);
     if (q < 0.f) ++c;
   }
   return c;
@@ -440,7 +444,7 @@ __device__ float spectral_radius(float* A, int n, int mc, float* vv, float* ww,
       continue;
     }
     const float alpha = -copysignf(sqrtf(tail + x1 * x1), x1);
-    const float inv = 1.0f / sqrtf(2.f * (alpha * alpha - alpha * x1));
+    const float inv = rsqrtf(2.f * (alpha * alpha - alpha * x1));
     for (int i = k + 1 + lane; i < n; i += 32)
       vv[i] = (i == k + 1 ? x1 - alpha : A[i * mc + k]) * inv;
     __syncwarp();
@@ -487,7 +491,7 @@ __device__ float spectral_radius(float* A, int n, int mc, float* vv, float* ww,
   bnd = warp_max_pos_f32(bnd);
   float lo = 0.f, hi = bnd * 1.0001f + 1e-20f;
   for (int round = 0; round < 6; ++round) {
-    const float step = (hi - lo) / 33.f;
+    const float step = (hi - lo) * (1.f / 33.f);
     const float sig = lo + step * (float)(lane + 1);
     const int cnt = (n - sturm_below(dd, ee, n, sig)) + sturm_below(dd, ee, n, -sig);
     const unsigned msk = __ballot_sync(kFull, cnt > 0);
@@ -502,20 +506,6 @@ __device__ float spectral_radius(float* A, int n, int mc, float* vv, float* ww,
     }
   }
   return 0.5f * (lo + hi);
-}
-
-// Number of eigenvalues below t of the tridiagonal (d, e2 = squared
-// off-diagonal), by the signs of the LDL^T pivots.
-__device__ __forceinline__ int sturm_count(const float* d, const float* e2, int n, float t) {
-  int c = 0;
-  float q = d[0] - t;
-  c += q < 0.f;
-  for (int i = 1; i < n; ++i) {
-    if (fabsf(q) < 1e-30f) q = -1e-30f;
-    q = d[i] - t - __fdividef(e2[i - 1], q);
-    c += q < 0.f;
-  }
-  return c;
 }
 
 // Largest |eigenvalue| of a symmetric n x n matrix (2 <= n <= kCapL) held as
@@ -540,7 +530,8 @@ __device__ float serial_rho(float* P, int n, float* sc) {
       e2[k] = x1 * x1;
       continue;
     }
-    const float alpha = -copysignf(sqrtf(tail + x1 * x1), x1);
+    const float nrm2 = tail + x1 * x1;
+    const float alpha = -copysignf(nrm2 * rsqrtf(nrm2), x1);
     const float inv = rsqrtf(2.f * (alpha * alpha - alpha * x1));
     // v (unit) in row k beyond the diagonal
     at(k, k + 1) = (x1 - alpha) * inv;
@@ -576,26 +567,60 @@ __device__ float serial_rho(float* P, int n, float* sc) {
     dmin = fminf(dmin, d[i]);
   }
   bnd = bnd * 1.0001f + 1e-20f;
-  // largest eigenvalue in [max d_i, bnd] (interlacing), smallest in [-bnd, min d_i]
-  float lo = dmax, hi = bnd;
-  for (int it = 0; it < 24; ++it) {
-    const float mid = 0.5f * (lo + hi);
-    if (sturm_count(d, e2, n, mid) == n)
-      hi = mid;
-    else
-      lo = mid;
+  // largest eigenvalue in [max d_i, bnd] (interlacing), smallest in
+  // [-bnd, min d_i]; both bracketed together, 4-ary: three shifts per end
+  // per round, six independent Sturm sequences interleaved.
+  float hl = dmax, hh = bnd, ll = -bnd, lh = dmin;
+  for (int it = 0; it < 12; ++it) {
+    float t[6], q[6];
+    int c[6];
+    const float hs = 0.25f * (hh - hl), ls = 0.25f * (lh - ll);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      t[k] = hl + hs * (float)(k + 1);
+      t[3 + k] = ll + ls * (float)(k + 1);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      q[k] = d[0] - t[k];
+      c[k] = q[k] < 0.f;
+    }
+    for (int i = 1; i < n; ++i) {
+      const float di = d[i], ei = e2[i - 1];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const float qk = fabsf(q[k]) < 1e-30f ? -1e-30f : q[k];
+        q[k] = di - t[k] - __fdividef(ei, qk);
+        c[k] += q[k] < 0.f;
+      }
+    }
+    // largest: lambda_max < t iff every eigenvalue is below t
+    if (c[0] == n) {
+      hh = t[0];
+    } else if (c[1] == n) {
+      hl = t[0];
+      hh = t[1];
+    } else if (c[2] == n) {
+      hl = t[1];
+      hh = t[2];
+    } else {
+      hl = t[2];
+    }
+    // smallest: lambda_min < t iff some eigenvalue is below t
+    if (c[3] >= 1) {
+      lh = t[3];
+    } else if (c[4] >= 1) {
+      ll = t[3];
+      lh = t[4];
+    } else if (c[5] >= 1) {
+      ll = t[4];
+      lh = t[5];
+    } else {
+      ll = t[5];
+    }
   }
-  const float lmax = 0.5f * (lo + hi);
-  lo = -bnd;
-  hi = dmin;
-  for (int it = 0; it < 24; ++it) {
-    const float mid = 0.5f * (lo + hi);
-    if (sturm_count(d, e2, n, mid) >= 1)
-      hi = mid;
-    else
-      lo = mid;
-  }
-  const float lmin = 0.5f * (lo + hi);
+  const float lmax = 0.5f * (hl + hh);
+  const float lmin = 0.5f * (ll + lh);
   return fmaxf(fabsf(lmax), fabsf(lmin));
 }
 
@@ -704,8 +729,9 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
       const float fm = (float)mult;
       hxy += fm * ent_term(C, T);
       const int ca = marg[a], cb = marg[b];
-      mi += fm * __fdividef((float)C, fT) *
-            log2f(__fdividef((float)((long long)C * T), (float)((long long)ca * cb)));
+      const long long ct = (long long)C * T, cc = (long long)ca * cb;
+      if (ct != cc)  // p = p_x p_y exactly contributes nothing
+        mi += fm * __fdividef((float)C, fT) * log2f(__fdividef((float)ct, (float)cc));
       atomicAdd(&sbin[i + j - 2 * w.lev0], 2 * n);
       atomicAdd(&dbin[j - i], 2 * n);
       if (dbg_glcm) {
@@ -730,8 +756,11 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
         // packed slot: A(a', b') = (C T - c_a c_b) / (T sqrt(c_a c_b))
         float* P = slots + di * kSlot;
         const int nn = nd * nd;
+        Magic mnd;
+        mnd.init((unsigned)nd);
+        const float invT = __fdividef(1.f, fT);
         for (int t = lane; t < nn; t += 32) {
-          const int ap = t / nd, bp = t - ap * nd;
+          const int ap = (int)mnd.div((unsigned)t), bp = t - ap * nd;
           if (bp < ap) continue;
           const int a = plist[ap], b = plist[bp];
           const int n = cnt[min(a, b) * mc + max(a, b)];
@@ -739,7 +768,7 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
           const int ca = marg[a], cb = marg[b];
           const long long num = (long long)C * T - (long long)ca * cb;
           P[ap * nd - ((ap * (ap - 1)) >> 1) + (bp - ap)] =
-              (float)num * rsqrtf((float)ca * (float)cb) / fT;
+              (float)num * rsqrtf((float)ca * (float)cb) * invT;
         }
         if (lane == 0) mn[di] = nd;
       } else {
@@ -754,7 +783,7 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
           if (ca && cb) {
             const int C = (a == b) ? 2 * n : n;
             const long long num = (long long)C * T - (long long)ca * cb;
-            v = (float)num * rsqrtf((float)ca * (float)cb) / fT;
+            v = __fdividef((float)num * rsqrtf((float)ca * (float)cb), fT);
           }
           S[a * mc + b] = v;
           S[b * mc + a] = v;
@@ -820,32 +849,29 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
     // one lane per feature
     float num = kNaNf, den = 1.f;
     const long long var_num = (long long)T * m2 - (long long)m1 * m1;  // T^2 sigma^2
-    switch (lane) {
-      case 0: num = (float)a1; den = fT; break;
-      case 1: num = (float)m1; den = fT; break;
-      case 2: num = fs[11]; den = fT * fT * fT * fT * fT; break;
-      case 3: num = i128_to_f32(ce3); den = fT * fT * fT * fT; break;
-      case 4: num = fs[10]; den = fT * fT * fT; break;
-      case 5: num = (float)dk2; den = fT; break;
-      case 6: num = (float)((long long)T * a1 - (long long)m1 * m1); den = (float)var_num; break;
-      case 7: num = (float)dk; den = fT; break;
-      case 8: num = fs[3]; break;
-      case 9: num = (float)((long long)T * dk2 - (long long)dk * dk); den = fT * fT; break;
-      case 10: num = (float)e2; den = fT * fT; break;
-      case 11: num = fs[1]; break;
-      case 12: num = -fs[2]; den = fs[0]; break;
-      case 13: num = sqrtf(fmaxf(0.f, -expm1f(-2.f * fs[2]))); break;
-      case 14: num = fs[4]; den = fT; break;
-      case 15: num = fs[5]; den = fT; break;
-      case 16: num = fs[6]; den = fT; break;
-      case 17: num = fs[7]; den = fT; break;
-      case 18: num = fs[8]; den = fT; break;
-      case 19: num = (float)maxc; den = fT; break;
-      case 20: num = (float)sk; den = fT; break;
-      case 21: num = fs[9]; break;
-      case 22: num = (float)var_num; den = fT * fT; break;
-      default: break;
-    }
+    if (lane == 0) { num = (float)a1; den = fT; }
+    if (lane == 1) { num = (float)m1; den = fT; }
+    if (lane == 2) { num = fs[11]; den = fT * fT * fT * fT * fT; }
+    if (lane == 3) { num = i128_to_f32(ce3); den = fT * fT * fT * fT; }
+    if (lane == 4) { num = fs[10]; den = fT * fT * fT; }
+    if (lane == 5) { num = (float)dk2; den = fT; }
+    if (lane == 6) { num = (float)((long long)T * a1 - (long long)m1 * m1); den = (float)var_num; }
+    if (lane == 7) { num = (float)dk; den = fT; }
+    if (lane == 8) { num = fs[3]; }
+    if (lane == 9) { num = (float)((long long)T * dk2 - (long long)dk * dk); den = fT * fT; }
+    if (lane == 10) { num = (float)e2; den = fT * fT; }
+    if (lane == 11) { num = fs[1]; }
+    if (lane == 12) { num = -fs[2]; den = fs[0]; }
+    if (lane == 13) { num = sqrtf(fmaxf(0.f, -expm1f(-2.f * fs[2]))); }
+    if (lane == 14) { num = fs[4]; den = fT; }
+    if (lane == 15) { num = fs[5]; den = fT; }
+    if (lane == 16) { num = fs[6]; den = fT; }
+    if (lane == 17) { num = fs[7]; den = fT; }
+    if (lane == 18) { num = fs[8]; den = fT; }
+    if (lane == 19) { num = (float)maxc; den = fT; }
+    if (lane == 20) { num = (float)sk; den = fT; }
+    if (lane == 21) { num = fs[9]; }
+    if (lane == 22) { num = (float)var_num; den = fT * fT; }
     acc_lane(A, 23, lane_quot(num, den));
   }
   __syncwarp();
@@ -968,25 +994,22 @@ __device__ void glrlm_family(const Win& w, const Arena& A, int32_t* dbg_glrlm) {
     warp_sum_f32x<7>(fs);
     const float N = (float)nr;
     float num = kNaNf, den = N;
-    switch (lane) {
-      case 0: num = fs[0]; break;
-      case 1: num = (float)sj2; break;
-      case 2: num = (float)glnu; break;
-      case 3: num = (float)glnu; den = N * N; break;
-      case 4: num = (float)rlnu; break;
-      case 5: num = (float)rlnu; den = N * N; break;
-      case 6: num = N; den = nvf; break;
-      case 7: num = (float)((long long)nr * si2 - (long long)si * si); den = N * N; break;
-      case 8: num = (float)((long long)nr * sj2 - (long long)sj * sj); den = N * N; break;
-      case 9: num = fs[6]; den = 1.f; break;
-      case 10: num = fs[1]; break;
-      case 11: num = (float)si2; break;
-      case 12: num = fs[2]; break;
-      case 13: num = fs[3]; break;
-      case 14: num = fs[4]; break;
-      case 15: num = fs[5]; break;
-      default: break;
-    }
+    if (lane == 0) { num = fs[0]; }
+    if (lane == 1) { num = (float)sj2; }
+    if (lane == 2) { num = (float)glnu; }
+    if (lane == 3) { num = (float)glnu; den = N * N; }
+    if (lane == 4) { num = (float)rlnu; }
+    if (lane == 5) { num = (float)rlnu; den = N * N; }
+    if (lane == 6) { num = N; den = nvf; }
+    if (lane == 7) { num = (float)((long long)nr * si2 - (long long)si * si); den = N * N; }
+    if (lane == 8) { num = (float)((long long)nr * sj2 - (long long)sj * sj); den = N * N; }
+    if (lane == 9) { num = fs[6]; den = 1.f; }
+    if (lane == 10) { num = fs[1]; }
+    if (lane == 11) { num = (float)si2; }
+    if (lane == 12) { num = fs[2]; }
+    if (lane == 13) { num = fs[3]; }
+    if (lane == 14) { num = fs[4]; }
+    if (lane == 15) { num = fs[5]; }
     acc_lane(A, 16, lane_quot(num, den));
   }
   acc_store(A, 16, 42);
@@ -1119,25 +1142,22 @@ __device__ void glszm_family(const Win& w, const Arena& A, int32_t* dbg_glszm) {
   const float N = (float)nz;
   const unsigned sj = (unsigned)w.nv;  // zone sizes add up to N_v
   float num = kNaNf, den = N;
-  switch (lane) {
-    case 0: num = fs[0]; break;
-    case 1: num = (float)sj2; break;
-    case 2: num = (float)glnu; break;
-    case 3: num = (float)glnu; den = N * N; break;
-    case 4: num = (float)sznu; break;
-    case 5: num = (float)sznu; den = N * N; break;
-    case 6: num = N; den = (float)w.nv; break;
-    case 7: num = (float)((long long)nz * si2 - (long long)si * si); den = N * N; break;
-    case 8: num = (float)((long long)nz * sj2 - (long long)sj * sj); den = N * N; break;
-    case 9: num = fs[6]; den = 1.f; break;
-    case 10: num = fs[1]; break;
-    case 11: num = (float)si2; break;
-    case 12: num = fs[2]; break;
-    case 13: num = fs[3]; break;
-    case 14: num = fs[4]; break;
-    case 15: num = fs[5]; break;
-    default: break;
-  }
+  if (lane == 0) { num = fs[0]; }
+  if (lane == 1) { num = (float)sj2; }
+  if (lane == 2) { num = (float)glnu; }
+  if (lane == 3) { num = (float)glnu; den = N * N; }
+  if (lane == 4) { num = (float)sznu; }
+  if (lane == 5) { num = (float)sznu; den = N * N; }
+  if (lane == 6) { num = N; den = (float)w.nv; }
+  if (lane == 7) { num = (float)((long long)nz * si2 - (long long)si * si); den = N * N; }
+  if (lane == 8) { num = (float)((long long)nz * sj2 - (long long)sj * sj); den = N * N; }
+  if (lane == 9) { num = fs[6]; den = 1.f; }
+  if (lane == 10) { num = fs[1]; }
+  if (lane == 11) { num = (float)si2; }
+  if (lane == 12) { num = fs[2]; }
+  if (lane == 13) { num = fs[3]; }
+  if (lane == 14) { num = fs[4]; }
+  if (lane == 15) { num = fs[5]; }
   if (lane < 16) A.fv[58 + lane] = lane_quot(num, den);
   __syncwarp();
 }
@@ -1244,23 +1264,20 @@ __device__ void gldm_ngtdm_family(const Win& w, const Arena& A, const FrJob& job
     warp_sum_f32x<7>(fs);
     const float fN = (float)N;
     float num = kNaNf, den = fN;
-    switch (lane) {
-      case 0: num = fs[0]; break;
-      case 1: num = (float)sj2; break;
-      case 2: num = (float)w.u2; break;
-      case 3: num = (float)dnu; break;
-      case 4: num = (float)dnu; den = fN * fN; break;
-      case 5: num = (float)((long long)N * si2 - (long long)si * si); den = fN * fN; break;
-      case 6: num = (float)((long long)N * sj2 - (long long)sj * sj); den = fN * fN; break;
-      case 7: num = fs[6]; den = 1.f; break;
-      case 8: num = fs[1]; break;
-      case 9: num = (float)si2; break;
-      case 10: num = fs[2]; break;
-      case 11: num = fs[3]; break;
-      case 12: num = fs[4]; break;
-      case 13: num = fs[5]; break;
-      default: break;
-    }
+    if (lane == 0) { num = fs[0]; }
+    if (lane == 1) { num = (float)sj2; }
+    if (lane == 2) { num = (float)w.u2; }
+    if (lane == 3) { num = (float)dnu; }
+    if (lane == 4) { num = (float)dnu; den = fN * fN; }
+    if (lane == 5) { num = (float)((long long)N * si2 - (long long)si * si); den = fN * fN; }
+    if (lane == 6) { num = (float)((long long)N * sj2 - (long long)sj * sj); den = fN * fN; }
+    if (lane == 7) { num = fs[6]; den = 1.f; }
+    if (lane == 8) { num = fs[1]; }
+    if (lane == 9) { num = (float)si2; }
+    if (lane == 10) { num = fs[2]; }
+    if (lane == 11) { num = fs[3]; }
+    if (lane == 12) { num = fs[4]; }
+    if (lane == 13) { num = fs[5]; }
     if (lane < 14) A.fv[74 + lane] = lane_quot(num, den);
   }
   __syncwarp();
@@ -1320,21 +1337,16 @@ __device__ void gldm_ngtdm_family(const Win& w, const Arena& A, const FrJob& job
     const float fv = (float)nvp, slsf = (float)sls * invL;
     float num = kNaNf, den = 1.f;
     if (nvp) {
-      switch (lane) {
-        case 0: num = fv; den = fs[0]; break;
-        case 1:
-          if (ngp == 1) {
+      if (lane == 0) { num = fv; den = fs[0]; }
+      if (lane == 1) { if (ngp == 1) {
             num = 0.f;
           } else {
             num = (float)c1 * slsf;
             den = fv * fv * (float)ngp * (float)(ngp - 1) * fv;
-          }
-          break;
-        case 2: num = fs[0]; den = (float)bden; break;
-        case 3: num = fs[1]; den = fv; break;
-        case 4: num = (float)str; den = fv * slsf; break;
-        default: break;
-      }
+          } }
+      if (lane == 2) { num = fs[0]; den = (float)bden; }
+      if (lane == 3) { num = fs[1]; den = fv; }
+      if (lane == 4) { num = (float)str; den = fv * slsf; }
     }
     if (lane < 5) A.fv[88 + lane] = (nvp == 0) ? kNaNf : lane_quot(num, den);
   }
