@@ -202,6 +202,32 @@ fr_status fr_batch_sync_status(fr_batch* b);
 fr_status fr_batch_last_kernel_ms(fr_batch* b, float* ms);
 void fr_batch_destroy(fr_batch* b);
 
+/* Allocation-free VOI voxel list.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory -- callers whose
+ * device memory already belongs to another allocator (a framework's caching
+ * pool, an application arena reserved at start-up) or that must not allocate
+ * while they run.  It writes into voi (device pointer, int32, room for
+ * `capacity` entries) the linear index (z*ny + y)*nx + x of every nonzero
+ * voxel of mask (device pointer, uint8 [nz][ny][nx]) in increasing order --
+ * the output column order of every map -- and their count into *n_voi (host).
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its only
+ * scratch is a fixed 2 MiB static device array (per-row counts and offsets)
+ * that every GPU loading the library holds until the process exits.
+ *   Limits: ny * nz <= FR_NOALLOC_MAX_ROWS and nx * ny * nz < 2^31, else
+ *   FR_ERR_UNSUPPORTED.  If the list does not fit in `capacity`, *n_voi still
+ *   receives the count, voi is left untouched and FR_ERR_INVALID_ARG returns.
+ *   `device` becomes the calling thread's current device.  The first call on
+ *   a device looks up the scratch's device address (once per device, with
+ *   that device current): make that first call before any stream capture.
+ *   Every call shares the scratch and overwrites every word of it that it
+ *   reads; calls that overlap on the GPU (other streams, other threads) race.
+ *   The call synchronises stream s once, to read the count; the list itself
+ *   is then written asynchronously on s. */
+enum { FR_NOALLOC_MAX_ROWS = 262144 };
+fr_status fr_voxel_list_noalloc(const uint8_t* mask, int32_t nx, int32_t ny, int32_t nz,
+                                int32_t* voi, int64_t capacity, int64_t* n_voi,
+                                int32_t device, fr_stream_t s);
+
 /* Names and helpers. */
 int32_t fr_feature_count(void);
 const char* fr_feature_name(int32_t id); /* NULL outside 0..92 */

@@ -309,6 +309,21 @@ def fr_batch_destroy(batch):
         batch.handle = None
 
 
+def fr_voxel_list_noalloc(mask, stream=None):
+    """Linear indices of the nonzero voxels of a uint8 CUDA mask [nz, ny, nx]
+    (z-major), computed without any device allocation by the library; the
+    output tensor is the caller's (allocated here by torch)."""
+    torch = _torch()
+    assert mask.is_cuda and mask.dtype == torch.uint8 and mask.is_contiguous()
+    nz, ny, nx = mask.shape
+    voi = torch.empty(mask.numel(), dtype=torch.int32, device=mask.device)
+    n = C.c_int64()
+    check("fr_voxel_list_noalloc", _lib.load().fr_voxel_list_noalloc(
+        C.c_void_p(mask.data_ptr()), nx, ny, nz, C.c_void_p(voi.data_ptr()), voi.numel(),
+        C.byref(n), mask.device.index or 0, _stream_ptr(stream)))
+    return voi[:n.value]
+
+
 def fr_feature_names():
     L = _lib.load()
     return [L.fr_feature_name(i).decode() for i in range(L.fr_feature_count())]

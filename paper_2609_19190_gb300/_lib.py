@@ -67,6 +67,8 @@ SIGNATURES = {
     "fr_batch_run": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), _P]),
     "fr_batch_sync_status": (C.c_int, [_P]),
     "fr_batch_destroy": (None, [_P]),
+    "fr_voxel_list_noalloc": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int64,
+                                        C.POINTER(C.c_int64), C.c_int32, _P]),
     "fr_feature_count": (C.c_int32, []),
     "fr_feature_name": (C.c_char_p, [C.c_int32]),
     "fr_status_string": (C.c_char_p, [C.c_int]),
