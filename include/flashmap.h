@@ -202,6 +202,32 @@ fr_status fr_batch_sync_status(fr_batch* b);
 fr_status fr_batch_last_kernel_ms(fr_batch* b, float* ms);
 void fr_batch_destroy(fr_batch* b);
 
+/* Continuous-batching server (iteration-level scheduling).  Requests are
+ * planned as they arrive (fr_server_add: synchronous, allocates the request's
+ * device state; mask, image and out are device pointers that must stay valid
+ * until the request is released).  Each fr_server_step launches the mapping
+ * kernel once over up to `voxel_budget` voxels taken round-robin from every
+ * request with work left, so a request added while others are being mapped
+ * joins the next step and shares its launches with them.  Steps run in order
+ * on the server's own stream, at most two in flight (a third waits for the
+ * oldest).  fr_server_poll reports finished requests (their maps are
+ * complete in `out`) with their status; fr_server_release frees a finished
+ * request's device memory and slot.  max_radius bounds the requests' kernel
+ * radius (it sizes the launch); max_slots bounds the requests held at once.
+ * A server is driven from one host thread. */
+typedef struct fr_server fr_server;
+fr_status fr_server_create(int32_t device, int32_t max_radius, int32_t max_slots,
+                           const fr_tune* tune, fr_server** out);
+fr_status fr_server_add(fr_server* s, const fr_map_params* p, const uint8_t* mask,
+                        const int16_t* image, float* out, int64_t* id);
+fr_status fr_server_step(fr_server* s, int64_t voxel_budget, int32_t* n_active);
+fr_status fr_server_poll(fr_server* s, int32_t wait, int64_t* done_ids, int32_t* done_status,
+                         int32_t cap, int32_t* n_done);
+fr_status fr_server_release(fr_server* s, int64_t id);
+fr_status fr_server_query(const fr_server* s, int32_t* active, int32_t* inflight_steps,
+                          size_t* device_bytes);
+void fr_server_destroy(fr_server* s);
+
 /* Allocation-free VOI voxel list.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory -- callers whose
  * device memory already belongs to another allocator (a framework's caching

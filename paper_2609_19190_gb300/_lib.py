@@ -69,6 +69,15 @@ SIGNATURES = {
     "fr_batch_destroy": (None, [_P]),
     "fr_voxel_list_noalloc": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int64,
                                         C.POINTER(C.c_int64), C.c_int32, _P]),
+    "fr_server_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(Tune),
+                                   C.POINTER(_P)]),
+    "fr_server_add": (C.c_int, [_P, C.POINTER(MapParams), _P, _P, _P, C.POINTER(C.c_int64)]),
+    "fr_server_step": (C.c_int, [_P, C.c_int64, C.POINTER(C.c_int32)]),
+    "fr_server_poll": (C.c_int, [_P, C.c_int32, _P, _P, C.c_int32, C.POINTER(C.c_int32)]),
+    "fr_server_release": (C.c_int, [_P, C.c_int64]),
+    "fr_server_query": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_size_t)]),
+    "fr_server_destroy": (None, [_P]),
     "fr_feature_count": (C.c_int32, []),
     "fr_feature_name": (C.c_char_p, [C.c_int32]),
     "fr_status_string": (C.c_char_p, [C.c_int]),

@@ -609,6 +609,101 @@ fr_status engine_open(Engine& E, const fr_map_params* ps, const uint8_t* const* 
   return st;
 }
 
+
+// ---------------------------------------------------------------------------
+// Server: iteration-level continuous batching.  Requests own their device
+// resources (a planned job); the server owns a job table of `max_slots`
+// entries, a launch configuration for windows up to `max_radius`, and a
+// stream.  Each step launches the persistent mapping kernel once over a
+// bounded number of voxels taken round-robin from every active request, so a
+// request that arrives while others are mapped joins the very next step and
+// its work shares the launches of the long-running ones.
+struct ServerReq {
+  JobRes job;
+  int64_t id = 0;
+  int slot = -1;
+  size_t issued = 0;     // items handed to launched steps
+  size_t completed = 0;  // items of completed steps
+  bool prepared = false;
+  bool done = false;
+  const int16_t* image = nullptr;
+  float* out = nullptr;
+};
+
+struct ServerStep {
+  cudaEvent_t ev = nullptr;
+  std::vector<std::pair<int, size_t>> advance;  // (slot, items) finished by this step
+  bool busy = false;
+};
+
+}  // namespace
+
+struct fr_server {
+  int device = 0, sms = 0, max_radius = 3, max_slots = 0;
+  fr_tune tune{};
+  FrArena arena{};
+  int nw = 0, stages = 0, tile_bytes = 0, smem = 0, grid = 0;
+  FrJob* jobs_dev = nullptr;
+  void** run_ptrs_dev = nullptr;
+  FrItem* items_dev[2] = {nullptr, nullptr};
+  int max_items = 0;
+  uint32_t* queue = nullptr;
+  int32_t* status = nullptr;
+  char* slab = nullptr;
+  int64_t slab_stride = 0;
+  int slab_ngc = 255;
+  cudaStream_t stream = nullptr;       // steps
+  cudaStream_t plan_stream = nullptr;  // request planning
+  uint32_t* prep_queue = nullptr;      // words the discretisation kernels reset,
+  int32_t* prep_status = nullptr;      // kept apart from the steps' queue/status
+  ServerStep steps[2];
+  int next_step = 0;
+  std::vector<ServerReq*> slots;
+  int64_t next_id = 1;
+  size_t bytes = 0;
+  std::vector<FrItem> host_items;
+};
+
+namespace {
+
+void server_release_all(fr_server* S) {
+  if (S->stream) cudaStreamSynchronize(S->stream);
+  for (auto*& r : S->slots)
+    if (r) {
+      r->job.release();
+      delete r;
+      r = nullptr;
+    }
+  for (auto& st : S->steps)
+    if (st.ev) cudaEventDestroy(st.ev);
+  cudaFree(S->jobs_dev);
+  cudaFree(S->run_ptrs_dev);
+  cudaFree(S->items_dev[0]);
+  cudaFree(S->items_dev[1]);
+  cudaFree(S->queue);
+  cudaFree(S->status);
+  cudaFree(S->slab);
+  cudaFree(S->prep_queue);
+  cudaFree(S->prep_status);
+  if (S->stream) cudaStreamDestroy(S->stream);
+  if (S->plan_stream) cudaStreamDestroy(S->plan_stream);
+}
+
+// Complete the oldest busy step if it has finished (or wait for it).
+fr_status server_complete(fr_server* S, ServerStep& st, bool wait) {
+  if (!st.busy) return FR_OK;
+  cudaError_t e = wait ? cudaEventSynchronize(st.ev) : cudaEventQuery(st.ev);
+  if (e == cudaErrorNotReady) return FR_OK;
+  if (e != cudaSuccess) return FR_ERR_CUDA;
+  for (auto& a : st.advance) {
+    ServerReq* r = S->slots[a.first];
+    if (r) r->completed += a.second;
+  }
+  st.advance.clear();
+  st.busy = false;
+  return FR_OK;
+}
+
 }  // namespace
 
 struct fr_plan {
@@ -920,6 +1015,302 @@ void fr_batch_destroy(fr_batch* b) {
   cudaSetDevice(b->E.device);
   b->E.release();
   delete b;
+}
+
+
+fr_status fr_server_create(int32_t device, int32_t max_radius, int32_t max_slots,
+                           const fr_tune* tune, fr_server** out) {
+  if (!out) return FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (max_radius < 1 || max_radius > kMaxRadius || max_slots < 1 || max_slots > 4096)
+    return FR_ERR_INVALID_ARG;
+  fr_server* S = new (std::nothrow) fr_server();
+  if (!S) return FR_ERR_OOM;
+  S->tune = default_tune(tune);
+  S->max_radius = max_radius;
+  S->max_slots = max_slots;
+  S->device = device;
+  fr_status st = FR_OK;
+  try {
+    if (!valid_tune(S->tune)) throw CudaFail{FR_ERR_INVALID_ARG};
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+      throw CudaFail{FR_ERR_UNSUPPORTED};
+    FR_TRY(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    FR_TRY(cudaGetDeviceProperties(&prop, device));
+    if (prop.major != 10 || prop.minor != 3) throw CudaFail{FR_ERR_UNSUPPORTED};
+    S->sms = prop.multiProcessorCount;
+    S->arena = fr_make_arena(max_radius);
+    const int hx = (max_radius + 3) / 4 * 4;
+    S->tile_bytes = fr_align((S->tune.brick_x + 2 * hx) * (S->tune.brick_y + 2 * max_radius) *
+                                 (S->tune.brick_z + 2 * max_radius) * 4,
+                             128);
+    S->stages = S->tune.stages;
+    S->nw = S->tune.consumer_warps;
+    int max_smem = 0;
+    FR_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    while (S->nw > 1 && fr_map_smem_bytes(S->stages, S->tile_bytes, S->nw, S->arena.bytes) > max_smem)
+      --S->nw;
+    S->smem = fr_map_smem_bytes(S->stages, S->tile_bytes, S->nw, S->arena.bytes);
+    if (S->smem > max_smem) throw CudaFail{FR_ERR_UNSUPPORTED};
+    FR_TRY(fr_map_configure(false, S->smem));
+    int blocks = 0;
+    FR_TRY(fr_map_occupancy(false, 32 * (S->nw + 1), S->smem, &blocks));
+    if (blocks < 1) throw CudaFail{FR_ERR_UNSUPPORTED};
+    if (S->tune.ctas_per_sm > 0) blocks = std::min(blocks, S->tune.ctas_per_sm);
+    S->grid = S->sms * blocks;
+    FR_TRY(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
+    FR_TRY(cudaStreamCreateWithFlags(&S->plan_stream, cudaStreamNonBlocking));
+    S->prep_queue = dev_alloc<uint32_t>(1, &S->bytes);
+    S->prep_status = dev_alloc<int32_t>(1, &S->bytes);
+    S->slab_stride = fr_align(fr_big_layout(S->slab_ngc, S->slab_ngc, S->arena.w_max).bytes, 256);
+    S->slab = dev_alloc<char>((size_t)S->grid * S->nw * S->slab_stride, &S->bytes);
+    FR_TRY(cudaMemsetAsync(S->slab, 0, (size_t)S->grid * S->nw * S->slab_stride, S->stream));
+    S->jobs_dev = dev_alloc<FrJob>(max_slots, &S->bytes);
+    S->run_ptrs_dev = dev_alloc<void*>(2 * (size_t)max_slots, &S->bytes);
+    S->max_items = 1 << 16;
+    S->items_dev[0] = dev_alloc<FrItem>(S->max_items, &S->bytes);
+    S->items_dev[1] = dev_alloc<FrItem>(S->max_items, &S->bytes);
+    S->queue = dev_alloc<uint32_t>(1, &S->bytes);
+    S->status = dev_alloc<int32_t>(1, &S->bytes);
+    FR_TRY(cudaMemsetAsync(S->status, 0, sizeof(int32_t), S->stream));
+    for (auto& stp : S->steps) FR_TRY(cudaEventCreateWithFlags(&stp.ev, cudaEventDisableTiming));
+    S->slots.assign(max_slots, nullptr);
+    FR_TRY(cudaStreamSynchronize(S->stream));
+  } catch (CudaFail& f) {
+    st = f.st;
+  }
+  if (st != FR_OK) {
+    server_release_all(S);
+    delete S;
+    return st;
+  }
+  *out = S;
+  return FR_OK;
+}
+
+fr_status fr_server_add(fr_server* S, const fr_map_params* p, const uint8_t* mask,
+                        const int16_t* image, float* out, int64_t* id) {
+  if (!S || !p || !mask || !image || !out || !id) return FR_ERR_INVALID_ARG;
+  if (!valid_params(p) || p->device != S->device) return FR_ERR_INVALID_ARG;
+  if (p->kernel_radius > S->max_radius) return FR_ERR_UNSUPPORTED;
+  int slot = -1;
+  for (int i = 0; i < S->max_slots; ++i)
+    if (!S->slots[i]) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) return FR_ERR_UNSUPPORTED;
+  if (cudaSetDevice(S->device) != cudaSuccess) return FR_ERR_CUDA;
+  ServerReq* r = new (std::nothrow) ServerReq();
+  if (!r) return FR_ERR_OOM;
+  fr_status st = build_job(p, mask, S->tune, r->job, S->plan_stream);
+  if (st != FR_OK) {
+    delete r;
+    return st;
+  }
+  try {
+    FrJob h;
+    memset((void*)&h, 0, sizeof(FrJob));
+    JobRes& j = r->job;
+    h.packed = j.packed;
+    h.voi = j.voi;
+    h.bcols = j.bcols;
+    h.state = j.state;
+    h.n_voi = j.n_voi;
+    h.nx = j.p.nx;
+    h.ny = j.p.ny;
+    h.nz = j.p.nz;
+    h.px = j.px;
+    h.r = j.p.kernel_radius;
+    h.delta = j.p.glcm_distance;
+    h.hx = (h.r + 3) / 4 * 4;
+    h.box_x = S->tune.brick_x + 2 * h.hx;
+    h.box_y = S->tune.brick_y + 2 * h.r;
+    h.box_z = S->tune.brick_z + 2 * h.r;
+    h.disc_mode = j.p.disc_mode;
+    h.bin_count = j.p.bin_count;
+    h.anchor_zero_floor = j.p.fbw_anchor == FR_ANCHOR_ZERO_FLOOR;
+    h.kurt_excess = j.p.kurtosis_excess ? 1 : 0;
+    h.nf = j.nf;
+    h.families = j.families;
+    h.bin_width = j.p.bin_width;
+    h.voxel_volume = j.p.spacing[0] * j.p.spacing[1] * j.p.spacing[2];
+    memcpy(h.row_of, j.row_of, sizeof(h.row_of));
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) throw CudaFail{FR_ERR_CUDA};
+    cuuint64_t gdim[3] = {(cuuint64_t)j.px, (cuuint64_t)j.p.ny, (cuuint64_t)j.p.nz};
+    cuuint64_t gstride[2] = {(cuuint64_t)j.px * 4, (cuuint64_t)j.px * j.p.ny * 4};
+    cuuint32_t box[3] = {(cuuint32_t)h.box_x, (cuuint32_t)h.box_y, (cuuint32_t)h.box_z};
+    cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&h.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, (void*)j.packed, gdim, gstride, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      throw CudaFail{FR_ERR_UNSUPPORTED};
+    void* ptrs[2] = {(void*)image, (void*)out};
+    FR_TRY(cudaMemcpyAsync(S->jobs_dev + slot, &h, sizeof(FrJob), cudaMemcpyHostToDevice,
+                           S->plan_stream));
+    FR_TRY(cudaMemcpyAsync(S->run_ptrs_dev + 2 * slot, ptrs, sizeof(ptrs),
+                           cudaMemcpyHostToDevice, S->plan_stream));
+    FR_TRY(cudaStreamSynchronize(S->plan_stream));
+  } catch (CudaFail& f) {
+    r->job.release();
+    delete r;
+    return f.st;
+  }
+  r->slot = slot;
+  r->id = S->next_id++;
+  r->image = image;
+  r->out = out;
+  S->slots[slot] = r;
+  *id = r->id;
+  return FR_OK;
+}
+
+fr_status fr_server_step(fr_server* S, int64_t voxel_budget, int32_t* n_active) {
+  if (!S || voxel_budget < 1) return FR_ERR_INVALID_ARG;
+  if (cudaSetDevice(S->device) != cudaSuccess) return FR_ERR_CUDA;
+  ServerStep& st = S->steps[S->next_step];
+  fr_status cs = server_complete(S, st, true);
+  if (cs != FR_OK) return cs;
+  // discretise and pack requests that joined since the last step
+  for (ServerReq* r : S->slots) {
+    if (!r || r->prepared) continue;
+    if (fr_launch_prepare(S->jobs_dev + r->slot, 1, r->job.n_voi, S->run_ptrs_dev + 2 * r->slot,
+                          S->prep_queue, S->prep_status, S->sms, S->stream) != cudaSuccess)
+      return FR_ERR_CUDA;
+    r->prepared = true;
+  }
+  // round-robin share of the voxel budget over the requests with work left
+  std::vector<ServerReq*> act;
+  for (ServerReq* r : S->slots)
+    if (r && r->issued < r->job.items.size()) act.push_back(r);
+  if (n_active) *n_active = (int32_t)act.size();
+  if (act.empty()) return FR_OK;
+  S->host_items.clear();
+  st.advance.clear();
+  int64_t left = voxel_budget;
+  std::vector<size_t> took(act.size(), 0);
+  bool progress = true;
+  while (left > 0 && progress && (int)S->host_items.size() < S->max_items) {
+    progress = false;
+    for (size_t k = 0; k < act.size() && left > 0; ++k) {
+      ServerReq* r = act[k];
+      const size_t at = r->issued + took[k];
+      if (at >= r->job.items.size() || (int)S->host_items.size() >= S->max_items) continue;
+      FrItem it = r->job.items[at];
+      it.job = r->slot;
+      S->host_items.push_back(it);
+      left -= it.n;
+      ++took[k];
+      progress = true;
+    }
+  }
+  for (size_t k = 0; k < act.size(); ++k) {
+    if (!took[k]) continue;
+    act[k]->issued += took[k];
+    st.advance.push_back({act[k]->slot, took[k]});
+  }
+  FrItem* items = S->items_dev[S->next_step];
+  if (cudaMemcpyAsync(items, S->host_items.data(), S->host_items.size() * sizeof(FrItem),
+                      cudaMemcpyHostToDevice, S->stream) != cudaSuccess ||
+      cudaMemsetAsync(S->queue, 0, sizeof(uint32_t), S->stream) != cudaSuccess)
+    return FR_ERR_CUDA;
+  FrMapArgs a{};
+  a.jobs = S->jobs_dev;
+  a.run_ptrs = S->run_ptrs_dev;
+  a.items = items;
+  a.n_items = (int32_t)S->host_items.size();
+  a.consumer_warps = S->nw;
+  a.stages = S->stages;
+  a.tile_bytes = S->tile_bytes;
+  a.queue = S->queue;
+  a.status = S->status;
+  a.slab = S->slab;
+  a.slab_stride = S->slab_stride;
+  a.slab_ngc = S->slab_ngc;
+  a.arena = S->arena;
+  a.timeout_ns = kTimeoutNs;
+  const int grid = std::min(S->grid, a.n_items);
+  if (fr_map_launch(false, a, grid, S->smem, S->stream) != cudaSuccess) return FR_ERR_CUDA;
+  if (cudaEventRecord(st.ev, S->stream) != cudaSuccess) return FR_ERR_CUDA;
+  st.busy = true;
+  S->next_step ^= 1;
+  return FR_OK;
+}
+
+fr_status fr_server_poll(fr_server* S, int32_t wait, int64_t* done_ids, int32_t* done_status,
+                         int32_t cap, int32_t* n_done) {
+  if (!S || !n_done || cap < 0 || (cap > 0 && (!done_ids || !done_status)))
+    return FR_ERR_INVALID_ARG;
+  if (cudaSetDevice(S->device) != cudaSuccess) return FR_ERR_CUDA;
+  *n_done = 0;
+  // steps complete in launch order
+  for (int k = 0; k < 2; ++k) {
+    ServerStep& st = S->steps[(S->next_step + k) & 1];
+    fr_status cs = server_complete(S, st, wait != 0);
+    if (cs != FR_OK) return cs;
+    if (st.busy) break;
+  }
+  int32_t dev_status = 0;
+  bool status_read = false;
+  for (ServerReq* r : S->slots) {
+    if (!r || r->done || !r->prepared || r->completed < r->job.items.size()) continue;
+    if (*n_done >= cap) break;
+    if (!status_read) {
+      if (cudaMemcpy(&dev_status, S->status, sizeof(dev_status), cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+        return FR_ERR_CUDA;
+      status_read = true;
+    }
+    FrJobState js;
+    if (cudaMemcpy(&js, r->job.state, sizeof(js), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return FR_ERR_CUDA;
+    r->done = true;
+    done_ids[*n_done] = r->id;
+    done_status[*n_done] = js.status ? js.status : dev_status;
+    ++*n_done;
+  }
+  return FR_OK;
+}
+
+fr_status fr_server_release(fr_server* S, int64_t id) {
+  if (!S) return FR_ERR_INVALID_ARG;
+  for (auto*& r : S->slots) {
+    if (!r || r->id != id) continue;
+    if (!r->done) return FR_ERR_INVALID_ARG;
+    if (cudaSetDevice(S->device) != cudaSuccess) return FR_ERR_CUDA;
+    cudaStreamSynchronize(S->stream);
+    r->job.release();
+    delete r;
+    r = nullptr;
+    return FR_OK;
+  }
+  return FR_ERR_INVALID_ARG;
+}
+
+fr_status fr_server_query(const fr_server* S, int32_t* active, int32_t* inflight,
+                          size_t* device_bytes) {
+  if (!S) return FR_ERR_INVALID_ARG;
+  int32_t a = 0;
+  size_t b = S->bytes;
+  for (ServerReq* r : S->slots)
+    if (r) {
+      ++a;
+      b += r->job.bytes;
+    }
+  if (active) *active = a;
+  if (inflight) *inflight = (S->steps[0].busy ? 1 : 0) + (S->steps[1].busy ? 1 : 0);
+  if (device_bytes) *device_bytes = b;
+  return FR_OK;
+}
+
+void fr_server_destroy(fr_server* S) {
+  if (!S) return;
+  cudaSetDevice(S->device);
+  server_release_all(S);
+  delete S;
 }
 
 int32_t fr_feature_count(void) { return kNumFeatures; }

@@ -164,3 +164,37 @@ def sample_voxels(mask, n, seed):
         return vox.astype(np.int64)
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(vox, size=n, replace=False)).astype(np.int64)
+
+
+SERVED_SHAPES = ((32, 64, 64), (64, 64, 64), (64, 128, 128), (128, 128, 128), (128, 256, 256))
+
+
+def served_requests(n, seed=200, median=50000.0, sigma=1.0, max_voxels=2000000,
+                    min_voxels=1000):
+    """Requests of the served workload: ellipsoidal VOIs of log-normal size
+    (median 50k voxels, sigma_ln 1.0, truncated to [1k, 2M]) with a random
+    aspect ratio, each in the smallest standard CT-like volume shape that holds
+    it; kernel radius uniform in {1, 2, 3}; FBN 64 or FBW 25 HU; all 93 maps.
+    Returns a list of dicts with keys shape, mask, radius, disc (parameter
+    overrides) and n_voi."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        target = float(np.clip(np.exp(rng.normal(np.log(median), sigma)), min_voxels, max_voxels))
+        aspect = rng.uniform(0.75, 1.25, size=3)
+        scale = (target / (4.0 / 3.0 * np.pi * np.prod(aspect))) ** (1.0 / 3.0)
+        semi = aspect * scale  # x, y, z
+        shape = SERVED_SHAPES[-1]
+        for sh in SERVED_SHAPES:
+            if semi[0] <= sh[2] / 2 - 1 and semi[1] <= sh[1] / 2 - 1 and semi[2] <= sh[0] / 2 - 1:
+                shape = sh
+                break
+        semi = np.minimum(semi, [shape[2] / 2 - 1, shape[1] / 2 - 1, shape[0] / 2 - 1])
+        centre = ((shape[2] - 1) / 2, (shape[1] - 1) / 2, (shape[0] - 1) / 2)
+        mask = ellipsoid(shape, centre, tuple(semi))
+        radius = int(rng.integers(1, 4))
+        disc = dict(disc_mode=0, bin_count=64) if rng.random() < 0.5 else \
+            dict(disc_mode=1, bin_width=25.0)
+        out.append(dict(shape=shape, mask=mask, radius=radius, disc=disc,
+                        n_voi=int(mask.sum())))
+    return out

@@ -1,0 +1,89 @@
+"""Continuous batching (fr_server_*): results are the same alone and in the
+mix, a request that arrives while a large one is being mapped finishes first,
+and admission waits for memory."""
+import numpy as np
+import pytest
+
+from paper_2609_19190_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _images(requests):
+    import torch
+    imgs = {}
+    for k, rq in enumerate(requests):
+        if rq["shape"] not in imgs:
+            imgs[rq["shape"]] = torch.from_numpy(synth.ct_like(rq["shape"], 400 + k)).cuda()
+    return imgs
+
+
+def _alone(rq, img):
+    import torch
+
+    import paper_2609_19190_gb300 as fm
+    nz, ny, nx = rq["shape"]
+    p = fm.fr_map_params_init(nx, ny, nz, kernel_radius=rq["radius"], **rq["disc"])
+    plan = fm.fr_map_plan(p, torch.from_numpy(rq["mask"]))
+    out = fm.fr_map_run(plan, img)
+    fm.fr_map_sync_status(plan)
+    return out
+
+
+def test_served_results_equal_alone_and_in_the_mix():
+    import torch
+
+    from paper_2609_19190_gb300 import serve
+    reqs = synth.served_requests(10, seed=5, median=6000.0, max_voxels=60000)
+    imgs = _images(reqs)
+    stats = serve.serve(reqs, imgs, rate=300.0, seed=1, voxel_budget=3000, keep_outputs=True)
+    assert stats["requests"] == len(reqs)
+    assert stats["steps"] > len(reqs)  # requests shared steps, more than one each
+    for i, rq in enumerate(reqs):
+        ref = _alone(rq, imgs[rq["shape"]])
+        got = stats["outputs"][i]
+        assert torch.equal(got.view(torch.int32), ref.view(torch.int32)), i
+    assert stats["p50_s"] <= stats["p99_s"]
+
+
+def test_late_small_request_overtakes_a_large_one():
+    import torch
+
+    import paper_2609_19190_gb300 as fm
+    from paper_2609_19190_gb300 import serve
+    big = synth.served_requests(1, seed=11, median=150000.0, sigma=0.01)[0]
+    small = synth.served_requests(1, seed=12, median=3000.0, sigma=0.01)[0]
+    imgs = _images([big, small])
+    srv = serve.Server()
+    outs = []
+    ids = []
+    for rq in (big, small):
+        nz, ny, nx = rq["shape"]
+        p = fm.fr_map_params_init(nx, ny, nz, kernel_radius=rq["radius"], **rq["disc"])
+        out = torch.empty((93, rq["n_voi"]), dtype=torch.float32, device="cuda")
+        outs.append(out)
+        ids.append(srv.add(p, rq["mask"], imgs[rq["shape"]], out))
+        if rq is big:
+            srv.step(4096)  # the big request is on the GPU when the small one arrives
+    order = []
+    while len(order) < 2:
+        srv.step(4096)
+        order += [rid for rid, st in srv.poll(wait=True)]
+    assert order[0] == ids[1] and order[1] == ids[0]
+    for rid in ids:
+        srv.release(rid)
+    srv.close()
+    for rq, out in zip((big, small), outs):
+        ref = _alone(rq, imgs[rq["shape"]])
+        assert torch.equal(out.view(torch.int32), ref.view(torch.int32))
+
+
+def test_admission_waits_for_memory():
+    from paper_2609_19190_gb300 import serve
+    reqs = synth.served_requests(6, seed=7, median=8000.0, max_voxels=40000)
+    imgs = _images(reqs)
+    est = [serve.request_bytes(r["shape"], r["n_voi"], 93) for r in reqs]
+    budget = int(max(est) * 1.5)
+    stats = serve.serve(reqs, imgs, rate=0.0, seed=2, voxel_budget=20000, hbm_budget=budget)
+    assert stats["requests"] == len(reqs)
+    assert stats["peak_admitted_bytes"] <= budget
