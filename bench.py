@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tune", default="", help="brick_x,brick_y,brick_z,vpi,warps,stages")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--batch-vois", type=int, default=64)
+    ap.add_argument("--served-requests", type=int, default=120)
+    ap.add_argument("--served-rates", default="10,50,100,200")
     return ap.parse_args()
 
 
@@ -222,11 +227,90 @@ def barrier(world):
 def max_over_ranks(v, world):
     if world == 1:
         return v
+    from paper_2609_19190_gb300 import dist as D
     import torch
-    import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return D.max_over_ranks(v, device=torch.device("cuda", torch.cuda.current_device()))
+
+
+# ------------------------------------------------------------------ batched / served
+def measure_batched(n_vois, dev, steps=3):
+    """64 CT-like 128x128x64 VOIs (log-uniform 4k-400k voxels, r in {1,2,3},
+    FBN 16/32/64, 93 maps): the plain path maps them one plan at a time; the
+    batched path maps all of them in one persistent launch (CUDA graph) with
+    the autotuner's launch shape.  Device time with CUDA events."""
+    import torch
+    import paper_2609_19190_gb300 as fm
+    from paper_2609_19190_gb300 import autotune, synth
+    params, masks, images = [], [], []
+    for i in range(n_vois):
+        img, mask, r, bins = synth.batch_item(i)
+        nz, ny, nx = img.shape
+        params.append(fm.fr_map_params_init(nx, ny, nz, disc_mode=0, bin_count=bins,
+                                            kernel_radius=r, device=dev.index or 0))
+        masks.append(torch.from_numpy(mask))
+        images.append(torch.from_numpy(img).to(dev))
+    voxels = int(sum(int(m.sum()) for m in masks))
+    tune, timings = autotune.pick(params, masks, images)
+    stream = torch.cuda.current_stream(dev)
+    plans = [fm.fr_map_plan(p, m) for p, m in zip(params, masks)]
+    outs = [torch.empty((pl.n_rows, pl.n_voi), dtype=torch.float32, device=dev) for pl in plans]
+    for pl, im, o in zip(plans, images, outs):
+        fm.fr_map_run(pl, im, o)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain_ms = []
+    for _ in range(steps):
+        e0.record(stream)
+        for pl, im, o in zip(plans, images, outs):
+            fm.fr_map_run(pl, im, o)
+        e1.record(stream)
+        e1.synchronize()
+        plain_ms.append(e0.elapsed_time(e1))
+    for pl in plans:
+        fm.fr_map_sync_status(pl)
+        fm.fr_map_destroy(pl)
+    b = fm.fr_batch_plan(params, masks, tune=tune)
+    fm.fr_batch_run(b, images, outs)
+    torch.cuda.synchronize(dev)
+    batch_ms = []
+    for _ in range(steps):
+        e0.record(stream)
+        fm.fr_batch_run(b, images, outs)
+        e1.record(stream)
+        e1.synchronize()
+        batch_ms.append(e0.elapsed_time(e1))
+    fm.fr_batch_sync_status(b)
+    fm.fr_batch_destroy(b)
+    tp, tb = statistics.median(plain_ms), statistics.median(batch_ms)
+    return {"value": voxels * 93 / (tb / 1e3), "unit": UNIT, "plain_value": voxels * 93 / (tp / 1e3),
+            "vs_plain": tp / tb, "ms_batched": tb, "ms_plain": tp, "n_vois": n_vois,
+            "voxels": voxels, "tune": tune, "launches_per_batch": 4,
+            "workload": "%d CT-like 128x128x64 VOIs, log-uniform 4k-400k voxels, r in {1,2,3}, "
+                        "FBN 16/32/64, 93 maps; batched = one persistent launch in a CUDA graph"
+                        % n_vois}
+
+
+def measure_served(n_requests, rates, dev):
+    """Poisson request stream (log-normal sizes, median 50k voxels), CT-like
+    volumes resident on the device, admission by free HBM, continuous
+    batching through fr_server_*; throughput and latency percentiles per rate."""
+    import torch
+    from paper_2609_19190_gb300 import serve, synth
+    reqs = synth.served_requests(n_requests, seed=200)
+    images = {sh: torch.from_numpy(synth.ct_like(sh, 500 + k)).to(dev)
+              for k, sh in enumerate(synth.SERVED_SHAPES)}
+    serve.serve(reqs[:8], images, rate=0.0, seed=0, device=dev.index or 0)  # warm-up
+    out = []
+    for rate in rates:
+        st = serve.serve(reqs, images, rate=rate, seed=3, voxel_budget=131072,
+                         device=dev.index or 0, time_limit=60)
+        out.append({"rate": rate, "throughput": st["throughput"], "p50_s": st["p50_s"],
+                    "p99_s": st["p99_s"], "requests": st["requests"],
+                    "makespan_s": st["makespan_s"]})
+    return {"unit": UNIT, "requests_per_rate": n_requests, "rates": out,
+            "workload": "Poisson arrivals; CT-like VOIs of log-normal size (median 50k voxels, "
+                        "sigma_ln 1, <= 2M), r in {1,2,3}, FBN 64 or FBW 25, 93 maps; "
+                        "continuous batching, 131072-voxel steps, admission by free HBM"}
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -378,6 +462,13 @@ def run_flashmap(args):
                           % (sms, ALU_LANES_PER_SM, sm_max),
             "hbm_gbs_achieved": (img.nbytes + 4 * nf * n_voi + 4 * n_voi) / kmean / 1e9,
             "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    batched = None
+    if not args.no_batched and args.workload == "ct_plain":
+        batched = measure_batched(args.batch_vois, dev)
+    served = None
+    if not args.no_served and args.workload == "ct_plain":
+        served = measure_served(args.served_requests,
+                                [float(r) for r in args.served_rates.split(",")], dev)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         rate, cores, n, dt, _ = oracle_rate(img, mask, kw, args.cpu_seconds)
@@ -394,6 +485,7 @@ def run_flashmap(args):
                    "launch": {"grid_note": "persistent, one producer + consumer warps per CTA",
                               "tune": tune}},
         "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+        "batched": batched, "served": served,
         "gpu_launches": 4 * args.steps,
     }
     print(json.dumps(line), flush=True)
