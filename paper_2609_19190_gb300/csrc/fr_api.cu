@@ -418,8 +418,10 @@ struct Engine {
       while (nw > 1 && fr_map_smem_bytes(stages, tile_bytes, nw, arena.bytes) > max_smem) --nw;
       smem = fr_map_smem_bytes(stages, tile_bytes, nw, arena.bytes);
       if (smem > max_smem) throw CudaFail{FR_ERR_UNSUPPORTED};
-      FR_TRY(fr_map_configure(false, smem));
-      FR_TRY(fr_map_configure(true, smem));
+      // the attribute is global to the kernel: raise it to the device's
+      // limit, so plans of different sizes can all launch
+      FR_TRY(fr_map_configure(false, max_smem));
+      FR_TRY(fr_map_configure(true, max_smem));
       int blocks = 0;
       FR_TRY(fr_map_occupancy(false, 32 * (nw + 1), smem, &blocks));
       if (blocks < 1) throw CudaFail{FR_ERR_UNSUPPORTED};
@@ -515,9 +517,14 @@ struct Engine {
     cudaError_t e = fr_launch_prepare(jobs_dev, (int)jobs.size(), max_voi, run_ptrs_dev, queue,
                                       status, sms, s);
     if (e != cudaSuccess) return e;
-    if ((e = cudaEventRecord(k_begin, s)) != cudaSuccess) return e;
+    // while capturing, external records stay timing records in the graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return e;
+    const unsigned flags =
+        cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if ((e = cudaEventRecordWithFlags(k_begin, s, flags)) != cudaSuccess) return e;
     if ((e = fr_map_launch(false, args(false), grid, smem, s)) != cudaSuccess) return e;
-    return cudaEventRecord(k_end, s);
+    return cudaEventRecordWithFlags(k_end, s, flags);
   }
 
   fr_status kernel_ms(float* ms) {
@@ -1054,7 +1061,8 @@ fr_status fr_server_create(int32_t device, int32_t max_radius, int32_t max_slots
       --S->nw;
     S->smem = fr_map_smem_bytes(S->stages, S->tile_bytes, S->nw, S->arena.bytes);
     if (S->smem > max_smem) throw CudaFail{FR_ERR_UNSUPPORTED};
-    FR_TRY(fr_map_configure(false, S->smem));
+    FR_TRY(fr_map_configure(false, max_smem));
+    FR_TRY(fr_map_configure(true, max_smem));
     int blocks = 0;
     FR_TRY(fr_map_occupancy(false, 32 * (S->nw + 1), S->smem, &blocks));
     if (blocks < 1) throw CudaFail{FR_ERR_UNSUPPORTED};
