@@ -567,11 +567,17 @@ __device__ float serial_rho(float* P, int n, float* sc) {
     dmin = fminf(dmin, d[i]);
   }
   bnd = bnd * 1.0001f + 1e-20f;
-  // largest eigenvalue in [max d_i, bnd] (interlacing), smallest in
-  // [-bnd, min d_i]; both bracketed together, 4-ary: three shifts per end
-  // per round, six independent Sturm sequences interleaved.
-  float hl = dmax, hh = bnd, ll = -bnd, lh = dmin;
-  for (int it = 0; it < 12; ++it) {
+  // A has the eigenvalue 0 (its null vector u), so lambda_max >= 0 >=
+  // lambda_min and the radius is max(lambda_max, -lambda_min).  Bracket both
+  // ends (lambda_max in [max d_i, bnd] by interlacing, lambda_min in
+  // [-bnd, min d_i]) with 4-ary Sturm bisection -- three shifts per end per
+  // round, six independent sequences interleaved -- until the brackets show
+  // which end decides the radius, then refine that end alone.
+  float hl = fmaxf(dmax, 0.f), hh = bnd, ll = -bnd, lh = fminf(dmin, 0.f);
+  constexpr int kRounds = 11;
+  int it = 0;
+  for (; it < kRounds; ++it) {
+    if (hl >= -ll || -lh >= hh) break;  // one end dominates
     float t[6], q[6];
     int c[6];
     const float hs = 0.25f * (hh - hl), ls = 0.25f * (lh - ll);
@@ -618,6 +624,44 @@ __device__ float serial_rho(float* P, int n, float* sc) {
     } else {
       ll = t[5];
     }
+  }
+  if (it < kRounds) {
+    // refine the dominant end only: as the largest eigenvalue of A or of -A
+    const bool top = hl >= -ll;
+    float lo = top ? hl : -lh, hi = top ? hh : -ll;
+    const float sg = top ? 1.f : -1.f;  // Sturm counts of -A at t: n - count(A, -t)
+    for (; it < kRounds; ++it) {
+      float t[3], q[3];
+      int c[3];
+      const float st = 0.25f * (hi - lo);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        t[k] = lo + st * (float)(k + 1);
+        q[k] = sg * d[0] - t[k];
+        c[k] = q[k] < 0.f;
+      }
+      for (int i = 1; i < n; ++i) {
+        const float di = sg * d[i], ei = e2[i - 1];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float qk = fabsf(q[k]) < 1e-30f ? -1e-30f : q[k];
+          q[k] = di - t[k] - __fdividef(ei, qk);
+          c[k] += q[k] < 0.f;
+        }
+      }
+      if (c[0] == n) {
+        hi = t[0];
+      } else if (c[1] == n) {
+        lo = t[0];
+        hi = t[1];
+      } else if (c[2] == n) {
+        lo = t[1];
+        hi = t[2];
+      } else {
+        lo = t[2];
+      }
+    }
+    return 0.5f * (lo + hi);
   }
   const float lmax = 0.5f * (hl + hh);
   const float lmin = 0.5f * (ll + lh);
