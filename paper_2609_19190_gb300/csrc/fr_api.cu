@@ -423,7 +423,7 @@ struct Engine {
       FR_TRY(fr_map_configure(false, max_smem));
       FR_TRY(fr_map_configure(true, max_smem));
       int blocks = 0;
-      FR_TRY(fr_map_occupancy(false, 32 * (nw + 1), smem, &blocks));
+      FR_TRY(fr_map_occupancy(false, 32 * nw, smem, &blocks));
       if (blocks < 1) throw CudaFail{FR_ERR_UNSUPPORTED};
       if (tune.ctas_per_sm > 0) blocks = std::min(blocks, tune.ctas_per_sm);
       grid = sms * blocks;
@@ -1064,7 +1064,7 @@ fr_status fr_server_create(int32_t device, int32_t max_radius, int32_t max_slots
     FR_TRY(fr_map_configure(false, max_smem));
     FR_TRY(fr_map_configure(true, max_smem));
     int blocks = 0;
-    FR_TRY(fr_map_occupancy(false, 32 * (S->nw + 1), S->smem, &blocks));
+    FR_TRY(fr_map_occupancy(false, 32 * S->nw, S->smem, &blocks));
     if (blocks < 1) throw CudaFail{FR_ERR_UNSUPPORTED};
     if (S->tune.ctas_per_sm > 0) blocks = std::min(blocks, S->tune.ctas_per_sm);
     S->grid = S->sms * blocks;

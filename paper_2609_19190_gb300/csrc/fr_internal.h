@@ -17,9 +17,9 @@ constexpr int kBinCap = 64;
 // GLCM MCC: directions whose present-level count is at most kCapL are solved
 // after the 13-direction loop, one lane per direction, from packed matrices
 // kept in per-direction slots of kSlot floats (packed upper triangle of
-// kCapL levels, then 3 scratch vectors; odd size spreads the banks).
+// kCapL levels, zero beyond the direction's own levels).
 constexpr int kCapL = 12;
-constexpr int kSlot = kCapL * (kCapL + 1) / 2 + 3 * kCapL + 1;
+constexpr int kSlot = kCapL * (kCapL + 1) / 2 + 1;  // odd: lanes hit distinct banks
 constexpr int kMaxConsumerWarps = 16;
 constexpr int kMaxStages = 4;
 

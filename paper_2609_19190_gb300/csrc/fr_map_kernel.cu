@@ -1,14 +1,15 @@
 // fr_map_kernel.cu -- the persistent mapping kernel.
 //
-// One CTA = 1 producer warp + NW consumer warps, resident for the whole
-// launch.  The producer pops work items (up to N voxels of one brick of one
-// VOI) from a device queue and stages each brick's halo -- a 3-D box of the
-// packed level/intensity volume -- into shared memory with one TMA tiled
-// load completing on an mbarrier; `stages` buffers let it run ahead.  Each
-// consumer warp maps whole voxels (fr_voxel.cuh) from the staged tile and
-// releases the buffer through a second mbarrier.  Every wait is bounded in
-// time; a wait that runs out records FR_ERR_TIMEOUT and the CTA leaves after
-// its own copies have landed.
+// One CTA = NW warps, resident for the whole launch; each warp maps whole
+// voxels (fr_voxel.cuh).  Work items (up to N voxels of one brick of one VOI)
+// come from a device queue; each item's brick halo -- a 3-D box of the packed
+// level/intensity volume -- is staged into shared memory by one TMA tiled
+// load completing on an mbarrier.  Thread 0 is the feeder: it claims the next
+// item and starts its load into a buffer as soon as every warp has gathered
+// its window from that buffer, so the copy overlaps the texture work of the
+// current item (`stages` buffers let it run further ahead).  No warp is set
+// aside for the copies.  Every wait is bounded in time; a wait that runs out
+// records FR_ERR_TIMEOUT and the CTA leaves after its own copies have landed.
 #include <cstdint>
 
 #include "fr_device.cuh"
@@ -57,11 +58,61 @@ __device__ __forceinline__ bool consumer_any(bool flag, int nthreads) {
   return r != 0;
 }
 
+// The feeder's state (meaningful in thread 0 only): which buffers hold a
+// copy that has not been waited for, and with which barrier parity.
+struct Feeder {
+  unsigned char* tiles;
+  uint64_t* full;
+  volatile int* slot;
+  int tile_bytes;
+  const CUtensorMap* last;
+  bool pending[kMaxStages];
+  unsigned ppar[kMaxStages];
+};
+
+// Thread 0: claim the next item (skipping VOIs whose preparation failed) and
+// start its halo copy into buffer `stage`, whose barrier phase `parity` it
+// completes; past the end of the queue the buffer gets the sentinel -1 and
+// the phase completes without a copy.
+__device__ __noinline__ void feed(const FrMapArgs& args, Feeder& fd, int stage,
+                                  unsigned parity) {
+  int it;
+  while (true) {
+    it = (int)atomicAdd(args.queue, 1u);
+    if (it >= args.n_items) {
+      it = -1;
+      break;
+    }
+    if (args.jobs[args.items[it].job].state->status == 0) break;
+  }
+  fd.slot[stage] = it;
+  if (it < 0) {
+    mbar_arrive(&fd.full[stage]);
+    return;
+  }
+  const FrItem& item = args.items[it];
+  const FrJob& job = args.jobs[item.job];
+  const CUtensorMap* tm = &job.tmap;
+  if (tm != fd.last) {
+    tmap_acquire(tm);
+    fd.last = tm;
+  }
+  const unsigned bytes = (unsigned)(job.box_x * job.box_y * job.box_z * 4);
+  mbar_arrive_expect_tx(&fd.full[stage], bytes);
+  tma_load_3d(fd.tiles + (size_t)stage * fd.tile_bytes, tm, item.bx - job.hx,
+              item.by - job.r, item.bz - job.r, &fd.full[stage]);
+  fd.pending[stage] = true;
+  fd.ppar[stage] = parity;
+}
+
 // Voxel t of the item, or no voxel (has == false: the warp only keeps step).
+// refill: this is the item's last round, so once every warp has gathered its
+// window the feeder reloads buffer `stage` (next barrier phase `parity`).
 template <bool DUMP>
 __device__ void map_voxel(const FrMapArgs& args, const FrJob& job,
                           const FrItem& item, const uint32_t* tile, int t, bool has,
-                          Arena& A, char* smem_big, char* slab_big, int it, int nt) {
+                          Arena& A, char* smem_big, char* slab_big, int it, int nt,
+                          Feeder& fd, bool refill, int stage, unsigned parity) {
   const int lane = lane_id();
   Win w;
   int col = 0;
@@ -128,6 +179,7 @@ __device__ void map_voxel(const FrMapArgs& args, const FrJob& job,
   }
   const bool work = has && !skip;
   consumer_bar(nt);
+  if (refill && threadIdx.x == 0) feed(args, fd, stage, parity);
   if (job.families & kFamGLCM) {
     if (work) glcm_family(w, A, job, d_glcm);
     consumer_bar(nt);
@@ -155,94 +207,37 @@ __device__ void map_voxel(const FrMapArgs& args, const FrJob& job,
 }
 
 template <bool DUMP>
-__global__ void __launch_bounds__(32 * (kMaxConsumerWarps + 1), 1)
+__global__ void __launch_bounds__(32 * kMaxConsumerWarps, 1)
     fr_map_kernel(const __grid_constant__ FrMapArgs args) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int S = args.stages, NW = args.consumer_warps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const CtaLayout cl = fr_cta_layout(S, args.tile_bytes, NW, args.arena.bytes);
-  uint64_t* full = (uint64_t*)(smem + cl.bars);
-  uint64_t* empty = full + S;
-  volatile int* slot = (volatile int*)(smem + cl.slots);
+  Feeder fd;
+  fd.tiles = smem + cl.tiles;
+  fd.full = (uint64_t*)(smem + cl.bars);
+  fd.slot = (volatile int*)(smem + cl.slots);
+  fd.tile_bytes = args.tile_bytes;
+  fd.last = nullptr;
+  for (int s = 0; s < kMaxStages; ++s) {
+    fd.pending[s] = false;
+    fd.ppar[s] = 0;
+  }
   const volatile int* abort_flag = args.status;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], NW);
-    }
+    for (int s = 0; s < S; ++s) mbar_init(&fd.full[s], 1);
     fence_mbar_init();
   }
-  if (warp < NW) {
-    // zero this warp's arena (the count matrices must start at zero)
+  // zero this warp's arena (the count matrices must start at zero)
+  {
     uint4* a = (uint4*)(smem + cl.arenas + warp * args.arena.bytes);
     for (int i = lane; i < args.arena.bytes / 16; i += 32) a[i] = make_uint4(0, 0, 0, 0);
   }
   __syncthreads();
+  if (threadIdx.x == 0)
+    for (int s = 0; s < S; ++s) feed(args, fd, s, 0u);
 
-  if (warp == NW) {
-    // ---------------------------------------------------------- producer
-    if (lane != 0) return;
-    int stage = 0;
-    unsigned phase = 0;
-    bool issued[kMaxStages];
-    unsigned ipar[kMaxStages];
-    for (int s = 0; s < kMaxStages; ++s) {
-      issued[s] = false;
-      ipar[s] = 0;
-    }
-    const CUtensorMap* last = nullptr;
-    bool failed = false;
-    while (true) {
-      int it = (int)atomicAdd(args.queue, 1u);
-      if (it >= args.n_items) it = -1;
-      const FrItem* item = nullptr;
-      const FrJob* job = nullptr;
-      if (it >= 0) {
-        item = &args.items[it];
-        job = &args.jobs[item->job];
-        if (job->state->status != 0) continue;  // job failed in preparation
-      }
-      if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, args.timeout_ns, abort_flag)) {
-        atomicCAS(args.status, 0, kStatusTimeout);
-        failed = true;
-        break;
-      }
-      slot[stage] = it;
-      if (it < 0) {
-        mbar_arrive(&full[stage]);
-        break;
-      }
-      const CUtensorMap* tm = &job->tmap;
-      if (tm != last) {
-        tmap_acquire(tm);
-        last = tm;
-      }
-      const unsigned bytes = (unsigned)(job->box_x * job->box_y * job->box_z * 4);
-      mbar_arrive_expect_tx(&full[stage], bytes);
-      tma_load_3d(smem + cl.tiles + (size_t)stage * args.tile_bytes, tm,
-                  item->bx - job->hx, item->by - job->r, item->bz - job->r,
-                  &full[stage]);
-      issued[stage] = true;
-      ipar[stage] = phase;
-      if (++stage == S) {
-        stage = 0;
-        phase ^= 1u;
-      }
-    }
-    // On the normal path every issued copy is consumed (consumers wait for
-    // it) before the CTA can finish.  After a failed wait the consumers may
-    // be gone: leave only after this CTA's own copies have landed (the last
-    // phase of each stage is then the last issue, so its parity is exact).
-    if (failed) {
-      const int zero = 0;
-      for (int s = 0; s < S; ++s)
-        if (issued[s]) mbar_wait_bounded(&full[s], ipar[s], args.timeout_ns, &zero);
-    }
-    return;
-  }
-
-  // ------------------------------------------------------------ consumers
   unsigned char* ab = smem + cl.arenas + warp * args.arena.bytes;
   Arena A;
   A.kb = (uint32_t*)(ab + args.arena.off_kb);
@@ -261,36 +256,37 @@ __global__ void __launch_bounds__(32 * (kMaxConsumerWarps + 1), 1)
   int stage = 0;
   unsigned phase = 0;
   while (true) {
-    const bool ok = mbar_wait_bounded(&full[stage], phase, args.timeout_ns, abort_flag);
-    // every consumer warp reaches this barrier; all leave together if any
-    // wait failed, so none is left waiting at a later barrier
+    const bool ok = mbar_wait_bounded(&fd.full[stage], phase, args.timeout_ns, abort_flag);
+    // every warp reaches this barrier; all leave together if any wait
+    // failed, so none is left waiting at a later barrier
     if (consumer_any(!ok, nt)) {
       if (!ok && lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
+      if (threadIdx.x == 0) {
+        // leave only after this CTA's own copies have landed
+        const int zero = 0;
+        for (int s = 0; s < S; ++s)
+          if (fd.pending[s]) mbar_wait_bounded(&fd.full[s], fd.ppar[s], args.timeout_ns, &zero);
+      }
       break;
     }
-    const int it = slot[stage];
-    if (it < 0) break;
+    if (threadIdx.x == 0) fd.pending[stage] = false;
+    const int it = fd.slot[stage];
+    if (it < 0) break;  // later buffers hold sentinels too: no copy in flight
     const FrItem item = args.items[it];
     const FrJob& job = args.jobs[item.job];
     const uint32_t* tile = (const uint32_t*)(smem + cl.tiles + (size_t)stage * args.tile_bytes);
     const int rounds = (item.n + NW - 1) / NW;
     for (int r = 0; r < rounds; ++r) {
       const int t = r * NW + warp;
-      map_voxel<DUMP>(args, job, item, tile, t, t < item.n, A, smem_big, slab_big, it, nt);
+      map_voxel<DUMP>(args, job, item, tile, t, t < item.n, A, smem_big, slab_big, it, nt, fd,
+                      r == rounds - 1, stage, phase ^ 1u);
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[stage]);
     if (++stage == S) {
       stage = 0;
       phase ^= 1u;
     }
   }
 }
-
-}  // namespace fr
-
-// Host launch helpers (C++ linkage, used by fr_api.cu).
-namespace fr {
 
 int fr_map_smem_bytes(int stages, int tile_bytes, int nw, int arena_bytes) {
   return fr_cta_layout(stages, tile_bytes, nw, arena_bytes).bytes;
@@ -308,7 +304,7 @@ cudaError_t fr_map_occupancy(bool dump, int threads, int smem_bytes, int* blocks
 
 cudaError_t fr_map_launch(bool dump, const FrMapArgs& args, int grid, int smem_bytes,
                           cudaStream_t s) {
-  const int threads = 32 * (args.consumer_warps + 1);
+  const int threads = 32 * args.consumer_warps;
   if (dump)
     fr_map_kernel<true><<<grid, threads, smem_bytes, s>>>(args);
   else

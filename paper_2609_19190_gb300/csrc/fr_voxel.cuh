@@ -508,164 +508,162 @@ __device__ float spectral_radius(float* A, int n, int mc, float* vv, float* ww,
   return 0.5f * (lo + hi);
 }
 
-// Largest |eigenvalue| of a symmetric n x n matrix (2 <= n <= kCapL) held as
-// a packed upper triangle P (row i holds columns i..n-1), by one thread:
-// Householder tridiagonalisation in place, then bisection of the largest
-// and the smallest eigenvalue with Sturm counts.  sc: 3 kCapL floats.
-__device__ float serial_rho(float* P, int n, float* sc) {
-  float* w = sc;
-  float* d = sc + kCapL;
-  float* e2 = sc + 2 * kCapL;
-  auto at = [&](int i, int j) -> float& { return P[i * n - ((i * (i - 1)) >> 1) + (j - i)]; };
-  auto sym = [&](int i, int j) -> float { return i <= j ? at(i, j) : at(j, i); };
-  for (int k = 0; k + 2 < n; ++k) {
-    const float x1 = at(k, k + 1);
-    float tail = 0.f;
-    for (int i = k + 2; i < n; ++i) {
-      const float x = at(k, i);
-      tail += x * x;
+// Index of (i, j), i <= j, in the packed upper triangle of an n x n matrix
+// (row i holds columns i..n-1).
+__host__ __device__ constexpr int pk(int n, int i, int j) {
+  return i * n - ((i * (i - 1)) >> 1) + (j - i);
+}
+
+// Sturm counts of the symmetric tridiagonal (d, e2 = squared off-diagonal)
+// times sg (+1 or -1) at K shifts t: c[k] = number of eigenvalues below t[k].
+template <int N, int K>
+__device__ __forceinline__ void sturm_counts(const float (&d)[N], const float (&e2)[N],
+                                             float sg, const float (&t)[K], int (&c)[K]) {
+  float q[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    q[k] = sg * d[0] - t[k];
+    c[k] = q[k] < 0.f;
+  }
+#pragma unroll
+  for (int i = 1; i < N; ++i) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float qk = fabsf(q[k]) < 1e-30f ? -1e-30f : q[k];
+      q[k] = sg * d[i] - t[k] - __fdividef(e2[i - 1], qk);
+      c[k] += q[k] < 0.f;
     }
-    if (tail == 0.f) {
-      d[k] = at(k, k);
-      e2[k] = x1 * x1;
-      continue;
-    }
-    const float nrm2 = tail + x1 * x1;
-    const float alpha = -copysignf(nrm2 * rsqrtf(nrm2), x1);
-    const float inv = rsqrtf(2.f * (alpha * alpha - alpha * x1));
-    // v (unit) in row k beyond the diagonal
-    at(k, k + 1) = (x1 - alpha) * inv;
-    for (int i = k + 2; i < n; ++i) at(k, i) *= inv;
-    float K = 0.f;
-    for (int i = k + 1; i < n; ++i) {
+  }
+}
+
+// New bracket [lo, hi] of the largest eigenvalue from the counts at the
+// three inner points of a 4-way split (largest < t iff every eigenvalue is).
+template <int N>
+__device__ __forceinline__ void narrow_top(const float (&t)[3], const int (&c)[3],
+                                           float& lo, float& hi) {
+  if (c[0] == N) {
+    hi = t[0];
+  } else if (c[1] == N) {
+    lo = t[0];
+    hi = t[1];
+  } else if (c[2] == N) {
+    lo = t[1];
+    hi = t[2];
+  } else {
+    lo = t[2];
+  }
+}
+
+// Largest |eigenvalue| of a symmetric N x N matrix read from a packed upper
+// triangle in the kCapL x kCapL layout, by one thread with every value in
+// registers.  Rows and columns beyond the matrix hold zeros: they only add
+// the eigenvalue 0, which every deflated matrix A = S - u u^T already has
+// (A u = 0), so the radius is unchanged and one fixed N serves all smaller
+// matrices.  Householder tridiagonalisation (indices are compile-time
+// constants, so the loops unroll into independent FMAs), then 4-ary Sturm
+// bisection of the two ends of the spectrum.
+template <int N>
+__device__ __forceinline__ float rho_reg(const float* __restrict__ P) {
+  constexpr int NP = N * (N + 1) / 2;
+  float a[NP];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = i; j < N; ++j) a[pk(N, i, j)] = P[pk(kCapL, i, j)];
+  float d[N], e2[N];
+#pragma unroll
+  for (int k = 0; k + 2 < N; ++k) {
+    // reflect x = A(k, k+1..N-1) onto alpha e_1, |alpha| = |x|
+    const float x1 = a[pk(N, k, k + 1)];
+    float nrm2 = x1 * x1;
+#pragma unroll
+    for (int i = k + 2; i < N; ++i) nrm2 = fmaf(a[pk(N, k, i)], a[pk(N, k, i)], nrm2);
+    const float sq = sqrtf(nrm2);
+    // |x - alpha e_1|^2 = 2 (|x|^2 + |x_1| |x|); a zero row keeps H = I
+    const float inv = nrm2 > 0.f ? rsqrtf(2.f * fmaf(fabsf(x1), sq, nrm2)) : 0.f;
+    d[k] = a[pk(N, k, k)];
+    e2[k] = nrm2;
+    a[pk(N, k, k + 1)] = (x1 + copysignf(sq, x1)) * inv;  // unit v, in row k
+#pragma unroll
+    for (int i = k + 2; i < N; ++i) a[pk(N, k, i)] *= inv;
+    // w = A v - (v^T A v) v on the trailing block; A <- A - 2 (v w^T + w v^T)
+    float w[N];
+    float Kv = 0.f;
+#pragma unroll
+    for (int i = k + 1; i < N; ++i) {
       float acc = 0.f;
-      for (int j = k + 1; j < n; ++j) acc += sym(i, j) * at(k, j);
+#pragma unroll
+      for (int j = k + 1; j < N; ++j)
+        acc = fmaf(a[i <= j ? pk(N, i, j) : pk(N, j, i)], a[pk(N, k, j)], acc);
       w[i] = acc;
-      K += at(k, i) * acc;
+      Kv = fmaf(a[pk(N, k, i)], acc, Kv);
     }
-    for (int i = k + 1; i < n; ++i) w[i] -= K * at(k, i);
-    for (int i = k + 1; i < n; ++i) {
-      const float vi = at(k, i), wi = w[i];
-      for (int j = i; j < n; ++j) at(i, j) -= 2.f * (vi * w[j] + wi * at(k, j));
-    }
-    d[k] = at(k, k);
-    e2[k] = alpha * alpha;
+#pragma unroll
+    for (int i = k + 1; i < N; ++i) w[i] = fmaf(-Kv, a[pk(N, k, i)], w[i]);
+#pragma unroll
+    for (int i = k + 1; i < N; ++i)
+#pragma unroll
+      for (int j = i; j < N; ++j)
+        a[pk(N, i, j)] = fmaf(-2.f * a[pk(N, k, i)], w[j],
+                              fmaf(-2.f * w[i], a[pk(N, k, j)], a[pk(N, i, j)]));
   }
-  if (n >= 2) {
-    d[n - 2] = at(n - 2, n - 2);
-    const float e = at(n - 2, n - 1);
-    e2[n - 2] = e * e;
-  }
-  d[n - 1] = at(n - 1, n - 1);
+  d[N - 2] = a[pk(N, N - 2, N - 2)];
+  e2[N - 2] = a[pk(N, N - 2, N - 1)] * a[pk(N, N - 2, N - 1)];
+  d[N - 1] = a[pk(N, N - 1, N - 1)];
+  e2[N - 1] = 0.f;
+  // Gershgorin bound of the tridiagonal
   float bnd = 0.f, dmax = d[0], dmin = d[0];
-  for (int i = 0; i < n; ++i) {
-    float r = fabsf(d[i]);
-    if (i > 0) r += sqrtf(e2[i - 1]);
-    if (i < n - 1) r += sqrtf(e2[i]);
+  float e[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) e[i] = sqrtf(e2[i]);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float r = fabsf(d[i]) + e[i];
+    if (i > 0) r += e[i - 1];
     bnd = fmaxf(bnd, r);
     dmax = fmaxf(dmax, d[i]);
     dmin = fminf(dmin, d[i]);
   }
   bnd = bnd * 1.0001f + 1e-20f;
-  // A has the eigenvalue 0 (its null vector u), so lambda_max >= 0 >=
-  // lambda_min and the radius is max(lambda_max, -lambda_min).  Bracket both
-  // ends (lambda_max in [max d_i, bnd] by interlacing, lambda_min in
-  // [-bnd, min d_i]) with 4-ary Sturm bisection -- three shifts per end per
-  // round, six independent sequences interleaved -- until the brackets show
-  // which end decides the radius, then refine that end alone.
+  // A has the eigenvalue 0, so lambda_max >= 0 >= lambda_min and the radius
+  // is max(lambda_max, -lambda_min).  Bracket both ends (lambda_max in
+  // [max d_i, bnd], lambda_min in [-bnd, min d_i], by interlacing) until the
+  // brackets show which end decides the radius, then refine that end alone.
   float hl = fmaxf(dmax, 0.f), hh = bnd, ll = -bnd, lh = fminf(dmin, 0.f);
   constexpr int kRounds = 11;
   int it = 0;
   for (; it < kRounds; ++it) {
     if (hl >= -ll || -lh >= hh) break;  // one end dominates
-    float t[6], q[6];
-    int c[6];
+    float th[3], tl[3];
+    int ch[3], cl[3];
     const float hs = 0.25f * (hh - hl), ls = 0.25f * (lh - ll);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      t[k] = hl + hs * (float)(k + 1);
-      t[3 + k] = ll + ls * (float)(k + 1);
+      th[k] = hl + hs * (float)(k + 1);
+      tl[k] = -lh + ls * (float)(k + 1);  // shifts of -A: -lambda_min is its largest
     }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      q[k] = d[0] - t[k];
-      c[k] = q[k] < 0.f;
-    }
-    for (int i = 1; i < n; ++i) {
-      const float di = d[i], ei = e2[i - 1];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const float qk = fabsf(q[k]) < 1e-30f ? -1e-30f : q[k];
-        q[k] = di - t[k] - __fdividef(ei, qk);
-        c[k] += q[k] < 0.f;
-      }
-    }
-    // largest: lambda_max < t iff every eigenvalue is below t
-    if (c[0] == n) {
-      hh = t[0];
-    } else if (c[1] == n) {
-      hl = t[0];
-      hh = t[1];
-    } else if (c[2] == n) {
-      hl = t[1];
-      hh = t[2];
-    } else {
-      hl = t[2];
-    }
-    // smallest: lambda_min < t iff some eigenvalue is below t
-    if (c[3] >= 1) {
-      lh = t[3];
-    } else if (c[4] >= 1) {
-      ll = t[3];
-      lh = t[4];
-    } else if (c[5] >= 1) {
-      ll = t[4];
-      lh = t[5];
-    } else {
-      ll = t[5];
-    }
+    sturm_counts<N, 3>(d, e2, 1.f, th, ch);
+    sturm_counts<N, 3>(d, e2, -1.f, tl, cl);
+    narrow_top<N>(th, ch, hl, hh);
+    float nl = -lh, nh = -ll;
+    narrow_top<N>(tl, cl, nl, nh);
+    lh = -nl;
+    ll = -nh;
   }
-  if (it < kRounds) {
-    // refine the dominant end only: as the largest eigenvalue of A or of -A
-    const bool top = hl >= -ll;
-    float lo = top ? hl : -lh, hi = top ? hh : -ll;
-    const float sg = top ? 1.f : -1.f;  // Sturm counts of -A at t: n - count(A, -t)
-    for (; it < kRounds; ++it) {
-      float t[3], q[3];
-      int c[3];
-      const float st = 0.25f * (hi - lo);
+  if (it == kRounds) return fmaxf(fabsf(0.5f * (hl + hh)), fabsf(0.5f * (ll + lh)));
+  const bool top = hl >= -ll;
+  const float sg = top ? 1.f : -1.f;
+  float lo = top ? hl : -lh, hi = top ? hh : -ll;
+  for (; it < kRounds; ++it) {
+    float t[3];
+    int c[3];
+    const float st = 0.25f * (hi - lo);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        t[k] = lo + st * (float)(k + 1);
-        q[k] = sg * d[0] - t[k];
-        c[k] = q[k] < 0.f;
-      }
-      for (int i = 1; i < n; ++i) {
-        const float di = sg * d[i], ei = e2[i - 1];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const float qk = fabsf(q[k]) < 1e-30f ? -1e-30f : q[k];
-          q[k] = di - t[k] - __fdividef(ei, qk);
-          c[k] += q[k] < 0.f;
-        }
-      }
-      if (c[0] == n) {
-        hi = t[0];
-      } else if (c[1] == n) {
-        lo = t[0];
-        hi = t[1];
-      } else if (c[2] == n) {
-        lo = t[1];
-        hi = t[2];
-      } else {
-        lo = t[2];
-      }
-    }
-    return 0.5f * (lo + hi);
+    for (int k = 0; k < 3; ++k) t[k] = lo + st * (float)(k + 1);
+    sturm_counts<N, 3>(d, e2, sg, t, c);
+    narrow_top<N>(t, c, lo, hi);
   }
-  const float lmax = 0.5f * (hl + hh);
-  const float lmin = 0.5f * (ll + lh);
-  return fmaxf(fabsf(lmax), fabsf(lmin));
+  return 0.5f * (lo + hi);
 }
 
 // ------------------------------------------------------------------ GLCM
@@ -797,22 +795,26 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
           mres[di] = kNaNf;
         }
       } else if (nd <= kCapL) {
-        // packed slot: A(a', b') = (C T - c_a c_b) / (T sqrt(c_a c_b))
+        // packed slot in the kCapL layout, zero beyond the nd present levels:
+        // A(a', b') = (C T - c_a c_b) / (T sqrt(c_a c_b))
         float* P = slots + di * kSlot;
-        const int nn = nd * nd;
-        Magic mnd;
-        mnd.init((unsigned)nd);
         const float invT = __fdividef(1.f, fT);
-        for (int t = lane; t < nn; t += 32) {
-          const int ap = (int)mnd.div((unsigned)t), bp = t - ap * nd;
-          if (bp < ap) continue;
-          const int a = plist[ap], b = plist[bp];
-          const int n = cnt[min(a, b) * mc + max(a, b)];
-          const int C = (a == b) ? 2 * n : n;
-          const int ca = marg[a], cb = marg[b];
-          const long long num = (long long)C * T - (long long)ca * cb;
-          P[ap * nd - ((ap * (ap - 1)) >> 1) + (bp - ap)] =
-              (float)num * rsqrtf((float)ca * (float)cb) * invT;
+        constexpr int NP = kCapL * (kCapL + 1) / 2;
+        for (int t = lane; t < NP; t += 32) {
+          int ap = 0;
+#pragma unroll
+          for (int r = 1; r < kCapL; ++r) ap += (t >= pk(kCapL, r, r));
+          const int bp = t - pk(kCapL, ap, ap) + ap;
+          float v = 0.f;
+          if (bp < nd) {
+            const int a = plist[ap], b = plist[bp];
+            const int n = cnt[min(a, b) * mc + max(a, b)];
+            const int C = (a == b) ? 2 * n : n;
+            const int ca = marg[a], cb = marg[b];
+            const long long num = (long long)C * T - (long long)ca * cb;
+            v = (float)num * rsqrtf((float)ca * (float)cb) * invT;
+          }
+          P[t] = v;
         }
         if (lane == 0) mn[di] = nd;
       } else {
@@ -920,10 +922,13 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
   }
   __syncwarp();
   if (want_mcc) {
-    if (lane < kNumDirs && mn[lane] >= 2) {
-      const int n = mn[lane];
-      float* P = slots + lane * kSlot;
-      mres[lane] = serial_rho(P, n, P + kCapL * (kCapL + 1) / 2);
+    // one register-resident size for the warp: the smallest that holds every
+    // direction's matrix (zero padding leaves the radius unchanged)
+    const int nl = (lane < kNumDirs) ? mn[lane] : 0;
+    const int nmax = __reduce_max_sync(kFull, nl);
+    if (nl >= 2) {
+      const float* P = slots + lane * kSlot;
+      mres[lane] = nmax <= 4 ? rho_reg<4>(P) : nmax <= 8 ? rho_reg<8>(P) : rho_reg<kCapL>(P);
     }
     __syncwarp();
     if (lane == 23) {
