@@ -673,7 +673,7 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
   const int m = w.m, mc = A.mc;
   int* cnt = (int*)(A.big + A.L.cnt);
   int* marg = (int*)(A.big + A.L.marg);
-  int* plist = (int*)(A.big + A.L.prank);
+  int* prank = (int*)(A.big + A.L.prank);  // rank of a present level
   int* sbin = (int*)(A.big + A.L.sbin);
   int* dbin = (int*)(A.big + A.L.dbin);
   float* vv = (float*)(A.big + A.L.vec);
@@ -746,13 +746,24 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
         }
       }
       const unsigned pb = __ballot_sync(kFull, c > 0);
-      if (c > 0) plist[present + __popc(pb & lanemask_lt())] = a;
+      if (c > 0) prank[a] = present + __popc(pb & lanemask_lt());
       present += __popc(pb);
     }
     m1 = redux_u32(m1);
     m2 = redux_u32(m2);
+    // MCC matrix of up to kCapL present levels: written by the entries pass
+    // into this direction's slot (zero first: the padding beyond them)
+    const bool slot = want_mcc && present >= 2 && present <= kCapL;
+    // counts are cleared as the entries pass reads them, unless the
+    // many-level MCC solve still needs them
+    const bool clear_now = !want_mcc || present <= kCapL;
+    float* P = slots + di * kSlot;
+    const float invT = __fdividef(1.f, fT);
+    if (slot)
+      for (int t = lane; t < kSlot; t += 32) P[t] = 0.f;
     __syncwarp();
-    // entries: linear sums, entropies, mutual information, sum / difference bins
+    // entries: linear sums, entropies, mutual information, sum / difference
+    // bins, the MCC slot
     unsigned a1 = 0, e2 = 0, maxc = 0;
     float hxy = 0.f, mi = 0.f;
     for (int t0 = 0; t0 < mm2; t0 += 32) {
@@ -761,7 +772,16 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
       const int a = (int)mm.div((unsigned)t), b = t - a * m;
       if (b < a) continue;
       const int n = cnt[a * mc + b];
-      if (!n) continue;
+      if (!n) {
+        // S - u u^T is dense: an empty pair of present levels is -u_a u_b
+        if (slot) {
+          const int ca = marg[a], cb = marg[b];
+          if (ca && cb)
+            P[pk(kCapL, prank[a], prank[b])] =
+                (float)(-(long long)ca * cb) * rsqrtf((float)ca * (float)cb) * invT;
+        }
+        continue;
+      }
       const unsigned i = A.lev[a], j = A.lev[b];
       const int C = (a == b) ? 2 * n : n;
       const unsigned mult = (a == b) ? 1u : 2u;
@@ -774,6 +794,11 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
       const long long ct = (long long)C * T, cc = (long long)ca * cb;
       if (ct != cc)  // p = p_x p_y exactly contributes nothing
         mi += fm * __fdividef((float)C, fT) * log2f(__fdividef((float)ct, (float)cc));
+      if (clear_now) cnt[a * mc + b] = 0;
+      // A(a', b') = (C T - c_a c_b) / (T sqrt(c_a c_b)) over present ranks
+      if (slot)
+        P[pk(kCapL, prank[a], prank[b])] =
+            (float)(ct - cc) * rsqrtf((float)ca * (float)cb) * invT;
       atomicAdd(&sbin[i + j - 2 * w.lev0], 2 * n);
       atomicAdd(&dbin[j - i], 2 * n);
       if (dbg_glcm) {
@@ -794,29 +819,8 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
           mn[di] = 0;
           mres[di] = kNaNf;
         }
-      } else if (nd <= kCapL) {
-        // packed slot in the kCapL layout, zero beyond the nd present levels:
-        // A(a', b') = (C T - c_a c_b) / (T sqrt(c_a c_b))
-        float* P = slots + di * kSlot;
-        const float invT = __fdividef(1.f, fT);
-        constexpr int NP = kCapL * (kCapL + 1) / 2;
-        for (int t = lane; t < NP; t += 32) {
-          int ap = 0;
-#pragma unroll
-          for (int r = 1; r < kCapL; ++r) ap += (t >= pk(kCapL, r, r));
-          const int bp = t - pk(kCapL, ap, ap) + ap;
-          float v = 0.f;
-          if (bp < nd) {
-            const int a = plist[ap], b = plist[bp];
-            const int n = cnt[min(a, b) * mc + max(a, b)];
-            const int C = (a == b) ? 2 * n : n;
-            const int ca = marg[a], cb = marg[b];
-            const long long num = (long long)C * T - (long long)ca * cb;
-            v = (float)num * rsqrtf((float)ca * (float)cb) * invT;
-          }
-          P[t] = v;
-        }
-        if (lane == 0) mn[di] = nd;
+      } else if (slot) {
+        if (lane == 0) mn[di] = nd;  // solved after the 13 directions
       } else {
         // many levels: warp-cooperative solve now, on S in place of the counts
         float* S = (float*)cnt;
@@ -840,17 +844,15 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
           mn[di] = 0;
           mres[di] = rho;
         }
+        __syncwarp();
+        for (int t = lane; t < mm2; t += 32) {
+          const int a = (int)mm.div((unsigned)t);
+          cnt[a * mc + (t - a * m)] = 0;
+        }
       }
     }
     __syncwarp();
-    for (int t = lane; t < mm2; t += 32) {
-      const int a = (int)mm.div((unsigned)t);
-      cnt[a * mc + (t - a * m)] = 0;
-    }
-    for (int a = lane; a < m; a += 32) {
-      marg[a] = 0;
-      plist[a] = 0;
-    }
+    for (int a = lane; a < m; a += 32) marg[a] = 0;
     // difference and sum distributions (bins relative to the smallest level)
     unsigned dk = 0, dk2 = 0, sk = 0;
     float de = 0.f, idm = 0.f, idmn = 0.f, idd = 0.f, idn = 0.f, iv = 0.f, se = 0.f,
