@@ -603,7 +603,9 @@ void ngtdm_features(const std::vector<double>& n, const std::vector<double>& s,
       double pi_ = p[i - 1], pj_ = p[j - 1];
       double d = (double)(i - j);
       c1 += pi_ * pj_ * d * d;
-      busy_den += std::fabs(i * pi_ - j * pj_);
+      /* |i p_i - j p_j| from the integer counts, so that a difference that
+       * vanishes exactly (i n_i = j n_j) is exactly zero */
+      busy_den += std::fabs((double)i * n[i - 1] - (double)j * n[j - 1]) / Nvp;
       cplx += std::fabs(d) * (pi_ * s[i - 1] + pj_ * s[j - 1]) / (pi_ + pj_);
       str += (pi_ + pj_) * d * d;
     }
@@ -751,18 +753,34 @@ void map_one(const fro_params* p, const Cube& c, int ng, double* f) {
   firstorder_features(x, g, ng, vvox, p->kurtosis_excess, f + 0);
 
   std::vector<double> M, per((size_t)FRO_NUM_DIRS * 24);
-  for (int d = 0; d < FRO_NUM_DIRS; ++d) {
-    glcm_counts(c, dirs[d], p->distance, ng, M);
-    glcm_features(M, ng, &per[(size_t)d * 24]);
-  }
-  average_dirs(per, FRO_NUM_DIRS, 24, f + 18);
+  if (p->aggregation == FRO_AGG_MERGED) {
+    /* one matrix: the sum of the 13 directional matrices */
+    std::vector<double> sum((size_t)ng * ng, 0.0);
+    for (int d = 0; d < FRO_NUM_DIRS; ++d) {
+      glcm_counts(c, dirs[d], p->distance, ng, M);
+      for (size_t k = 0; k < sum.size(); ++k) sum[k] += M[k];
+    }
+    glcm_features(sum, ng, f + 18);
+    std::vector<double> rsum((size_t)ng * c.s, 0.0);
+    for (int d = 0; d < FRO_NUM_DIRS; ++d) {
+      glrlm_counts(c, dirs[d], ng, M);
+      for (size_t k = 0; k < rsum.size(); ++k) rsum[k] += M[k];
+    }
+    rl_features(rsum, ng, c.s, FRO_NUM_DIRS * nv, f + 42);
+  } else {
+    for (int d = 0; d < FRO_NUM_DIRS; ++d) {
+      glcm_counts(c, dirs[d], p->distance, ng, M);
+      glcm_features(M, ng, &per[(size_t)d * 24]);
+    }
+    average_dirs(per, FRO_NUM_DIRS, 24, f + 18);
 
-  per.assign((size_t)FRO_NUM_DIRS * 16, 0.0);
-  for (int d = 0; d < FRO_NUM_DIRS; ++d) {
-    glrlm_counts(c, dirs[d], ng, M);
-    rl_features(M, ng, c.s, nv, &per[(size_t)d * 16]);
+    per.assign((size_t)FRO_NUM_DIRS * 16, 0.0);
+    for (int d = 0; d < FRO_NUM_DIRS; ++d) {
+      glrlm_counts(c, dirs[d], ng, M);
+      rl_features(M, ng, c.s, nv, &per[(size_t)d * 16]);
+    }
+    average_dirs(per, FRO_NUM_DIRS, 16, f + 42);
   }
-  average_dirs(per, FRO_NUM_DIRS, 16, f + 42);
 
   glszm_counts(c, ng, M);
   rl_features(M, ng, c.s * c.s * c.s, nv, f + 58);
@@ -781,6 +799,7 @@ bool params_ok(const fro_params* p) {
   if (p->disc_mode == FRO_FBN && p->bin_count < 1) return false;
   if (p->disc_mode == FRO_FBW && !(p->bin_width > 0)) return false;
   if (p->disc_mode != FRO_FBN && p->disc_mode != FRO_FBW) return false;
+  if (p->aggregation != FRO_AGG_AVERAGE && p->aggregation != FRO_AGG_MERGED) return false;
   return true;
 }
 

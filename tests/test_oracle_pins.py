@@ -385,6 +385,12 @@ def test_ngtdm_constant_and_two_level():
     assert f[2] == pytest.approx(sps / (2 * abs(p1 - 2 * p2)))
     assert f[3] == pytest.approx(2 * (p1 * s1 + p2 * s2) / (p1 + p2) / N)
     assert f[4] == pytest.approx(2 * (p1 + p2) / (s1 + s2))
+    # levels 2 and 3 with n = (3, 2): 2 p_2 = 3 p_3 exactly, so busyness has a
+    # zero denominator and is undefined, although 2 (0.6) - 3 (0.4) is not 0
+    # in binary floating point
+    f = O.ngtdm_features(np.array([0.0, 3.0, 2.0]), np.array([0.0, 1.5, 2.5]))
+    assert 2 * 0.6 - 3 * 0.4 != 0.0
+    assert math.isnan(f[2]) and math.isfinite(f[0]) and math.isfinite(f[4])
 
 
 def test_firstorder_closed_form_ramp():
@@ -452,6 +458,49 @@ def test_map_equals_scalar_when_window_covers_voi():
     scalar = NP.features_of_cube(cube, raw, ng)
     for k in range(maps.shape[1]):
         np.testing.assert_allclose(maps[:, k], scalar, rtol=1e-9, atol=1e-9, equal_nan=True)
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_merged_maps_against_naive_enumerator(r):
+    rng = np.random.default_rng(40 + r)
+    img = rng.integers(0, 60, size=(6, 7, 6)).astype(np.int16)
+    mask = (rng.random(img.shape) < 0.75).astype(np.uint8)
+    maps, vox, levels, ng = _oracle_maps(img, mask, disc_mode=O.FBN, bin_count=5,
+                                         radius=r, aggregation=O.AGG_MERGED)
+    ref = NP.map_voxels(levels, img, ng, vox, r, merged=True)
+    np.testing.assert_allclose(maps, ref, rtol=1e-9, atol=1e-8, equal_nan=True)
+
+
+def test_merged_linear_features_are_weighted_direction_means():
+    # A feature linear in p = M / sum(M) over the merged matrix sum_d M_d is
+    # the mean of the per-direction values weighted by each direction's total
+    # (pairs for GLCM, runs for GLRLM); RunPercentage sum_d N_d / (13 N_v)
+    # is exactly the plain direction mean.
+    rng = np.random.default_rng(44)
+    img = rng.integers(0, 90, size=(7, 7, 7)).astype(np.int16)
+    mask = (rng.random(img.shape) < 0.7).astype(np.uint8)
+    kw = dict(disc_mode=O.FBN, bin_count=7, radius=2)
+    mrg, vox, levels, ng = _oracle_maps(img, mask, aggregation=O.AGG_MERGED, **kw)
+    avg, _, _, _ = _oracle_maps(img, mask, **kw)
+    p = O.make_params(img.shape, **kw)
+    lin_glcm = [18, 19, 23, 25, 32, 33, 34, 35, 36, 38]
+    lin_glrlm = [42, 43, 52, 53, 54, 55, 56, 57]
+    for k in range(0, len(vox), 7):
+        mats = O.matrices(p, levels, ng, vox[k])
+        nv = int(mats["hist"].sum())
+        T = mats["glcm"].reshape(13, -1).sum(1).astype(np.float64)
+        fg = np.array([O.glcm_features(mats["glcm"][d]) for d in range(13)])
+        ok = T > 0
+        want = (T[ok, None] * fg[ok][:, [f - 18 for f in lin_glcm]]).sum(0) / T[ok].sum()
+        np.testing.assert_allclose(mrg[lin_glcm, k], want, rtol=1e-10, atol=1e-12)
+        N = mats["glrlm"].reshape(13, -1).sum(1).astype(np.float64)
+        fr = np.array([O.glrlm_features(mats["glrlm"][d], nv) for d in range(13)])
+        want = (N[:, None] * fr[:, [f - 42 for f in lin_glrlm]]).sum(0) / N.sum()
+        np.testing.assert_allclose(mrg[lin_glrlm, k], want, rtol=1e-10, atol=1e-12)
+        assert mrg[48, k] == pytest.approx(avg[48, k], rel=1e-12)
+    # families without a direction are the same in both modes
+    np.testing.assert_array_equal(mrg[:18], avg[:18])
+    np.testing.assert_array_equal(mrg[58:], avg[58:])
 
 
 def test_map_flip_permutation_translation_equivariance():
