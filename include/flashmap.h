@@ -65,6 +65,14 @@ typedef enum fr_status {
 
 enum { FR_FBN = 0, FR_FBW = 1 };                             /* discretisation */
 enum { FR_ANCHOR_VOI_MIN = 0, FR_ANCHOR_ZERO_FLOOR = 1 };    /* FBW bin anchor  */
+/* Texture aggregation over the 13 directions (IBSI 3D:avg / 3D:mrg; the
+ * paper's IBSI configurations fix it per family, "IBSI compliance tests").
+ * AVERAGE: GLCM and GLRLM features per direction, mean over the non-empty
+ * directions.  MERGED: the 13 directional matrices are summed first and the
+ * features taken once; GLRLM RunPercentage then divides by 13 N_v (each
+ * voxel lies on one run per direction).  GLSZM, GLDM and NGTDM do not
+ * depend on a direction. */
+enum { FR_AGG_AVERAGE = 0, FR_AGG_MERGED = 1 };
 enum { FR_NUM_FEATURES = 93, FR_NUM_DIRECTIONS = 13, FR_MAX_RADIUS = 7 };
 
 /* Feature id ranges (ids are stable; names from fr_feature_name). */
@@ -88,7 +96,7 @@ typedef struct fr_map_params {
   int32_t kurtosis_excess;  /* 1: m4/m2^2 - 3 (IBSI; default); 0: m4/m2^2         */
   int32_t device;           /* CUDA device ordinal                                */
   int32_t mask_on_device;   /* 1: the mask pointer is a device pointer; 0: host   */
-  int32_t reserved;         /* must be 0                                          */
+  int32_t aggregation;      /* FR_AGG_AVERAGE (default) or FR_AGG_MERGED          */
 } fr_map_params;
 
 /* Launch shape of the mapping kernel (the autotuner's knobs).  Zero fields

@@ -34,6 +34,12 @@ extern "C" {
 
 enum { FRO_FBN = 0, FRO_FBW = 1 };
 enum { FRO_ANCHOR_VOI_MIN = 0, FRO_ANCHOR_ZERO_FLOOR = 1 };
+/* Aggregation of the direction-dependent families (GLCM, GLRLM) over the
+ * 13 directions: AVERAGE takes features per direction and averages them;
+ * MERGED sums the 13 matrices and takes the features once (IBSI 3D:avg and
+ * 3D:mrg; the IBSI configurations of the paper's compliance tests name one
+ * per family).  Merged GLRLM run percentage divides by 13 N_v. */
+enum { FRO_AGG_AVERAGE = 0, FRO_AGG_MERGED = 1 };
 
 #define FRO_NUM_FEATURES 93
 #define FRO_NUM_DIRS 13
@@ -48,6 +54,7 @@ typedef struct fro_params {
   int32_t radius;            /* window radius r (Chebyshev), 1..7            */
   int32_t distance;          /* GLCM offset distance delta (>= 1)            */
   int32_t kurtosis_excess;   /* 1: m4/m2^2 - 3 ; 0: m4/m2^2                  */
+  int32_t aggregation;       /* FRO_AGG_AVERAGE or FRO_AGG_MERGED            */
 } fro_params;
 
 /* Number of features and the name of feature id (0..92). */

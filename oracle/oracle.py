@@ -15,6 +15,7 @@ NUM_FEATURES = 93
 NUM_DIRS = 13
 FBN, FBW = 0, 1
 ANCHOR_VOI_MIN, ANCHOR_ZERO_FLOOR = 0, 1
+AGG_AVERAGE, AGG_MERGED = 0, 1
 
 
 class Params(C.Structure):
@@ -24,13 +25,13 @@ class Params(C.Structure):
         ("disc_mode", C.c_int32), ("bin_count", C.c_int32),
         ("bin_width", C.c_double), ("fbw_anchor", C.c_int32),
         ("radius", C.c_int32), ("distance", C.c_int32),
-        ("kurtosis_excess", C.c_int32),
+        ("kurtosis_excess", C.c_int32), ("aggregation", C.c_int32),
     ]
 
 
 def make_params(shape, *, disc_mode=FBN, bin_count=16, bin_width=25.0,
                 fbw_anchor=ANCHOR_VOI_MIN, radius=1, distance=1,
-                spacing=(1.0, 1.0, 1.0), kurtosis_excess=1):
+                spacing=(1.0, 1.0, 1.0), kurtosis_excess=1, aggregation=0):
     nz, ny, nx = shape
     p = Params()
     p.nx, p.ny, p.nz = nx, ny, nz
@@ -38,6 +39,7 @@ def make_params(shape, *, disc_mode=FBN, bin_count=16, bin_width=25.0,
     p.disc_mode, p.bin_count, p.bin_width = disc_mode, bin_count, bin_width
     p.fbw_anchor, p.radius, p.distance = fbw_anchor, radius, distance
     p.kurtosis_excess = kurtosis_excess
+    p.aggregation = aggregation
     return p
 
 

@@ -30,7 +30,7 @@ class MapParams(C.Structure):
         ("kernel_radius", C.c_int32), ("glcm_distance", C.c_int32),
         ("feature_mask", C.c_uint64 * 2),
         ("kurtosis_excess", C.c_int32), ("device", C.c_int32),
-        ("mask_on_device", C.c_int32), ("reserved", C.c_int32),
+        ("mask_on_device", C.c_int32), ("aggregation", C.c_int32),
     ]
 
 

@@ -152,7 +152,7 @@ bool valid_params(const fr_map_params* p) {
     return false;
   }
   if (!(p->spacing[0] > 0 && p->spacing[1] > 0 && p->spacing[2] > 0)) return false;
-  if (p->reserved != 0) return false;
+  if (p->aggregation != FR_AGG_AVERAGE && p->aggregation != FR_AGG_MERGED) return false;
   bool any = false;
   for (int f = 0; f < kNumFeatures; ++f)
     if ((p->feature_mask[f >> 6] >> (f & 63)) & 1ull) any = true;
@@ -455,6 +455,7 @@ struct Engine {
         h.px = j.px;
         h.r = j.p.kernel_radius;
         h.delta = j.p.glcm_distance;
+        h.agg = j.p.aggregation;
         h.hx = (h.r + 3) / 4 * 4;
         h.box_x = tune.brick_x + 2 * h.hx;
         h.box_y = tune.brick_y + 2 * h.r;
@@ -744,7 +745,7 @@ void fr_map_params_init(fr_map_params* p, int32_t nx, int32_t ny, int32_t nz) {
   p->kurtosis_excess = 1;
   p->device = 0;
   p->mask_on_device = 0;
-  p->reserved = 0;
+  p->aggregation = FR_AGG_AVERAGE;
 }
 
 fr_status fr_map_plan(const fr_map_params* p, const uint8_t* mask, const fr_tune* tune,
@@ -1133,6 +1134,7 @@ fr_status fr_server_add(fr_server* S, const fr_map_params* p, const uint8_t* mas
     h.px = j.px;
     h.r = j.p.kernel_radius;
     h.delta = j.p.glcm_distance;
+    h.agg = j.p.aggregation;
     h.hx = (h.r + 3) / 4 * 4;
     h.box_x = S->tune.brick_x + 2 * h.hx;
     h.box_y = S->tune.brick_y + 2 * h.r;

@@ -55,6 +55,7 @@ struct alignas(128) FrJob {
   int32_t box_x, box_y, box_z;
   int32_t disc_mode, bin_count, anchor_zero_floor;
   int32_t kurt_excess;
+  int32_t agg;  // FR_AGG_AVERAGE / FR_AGG_MERGED
   int32_t nf;  // output rows
   uint32_t families;
   double bin_width;

@@ -185,7 +185,7 @@ __device__ void map_voxel(const FrMapArgs& args, const FrJob& job,
     consumer_bar(nt);
   }
   if (job.families & kFamGLRLM) {
-    if (work) glrlm_family(w, A, d_glrlm);
+    if (work) glrlm_family(w, A, job.agg == 1, d_glrlm);
     consumer_bar(nt);
   }
   if (job.families & kFamGLSZM) {

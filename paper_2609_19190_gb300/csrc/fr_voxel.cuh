@@ -666,6 +666,19 @@ __device__ __forceinline__ float rho_reg(const float* __restrict__ P) {
   return 0.5f * (lo + hi);
 }
 
+// (1 + d) ln(1 + d) - d >= 0 (d >= -1) without the cancellation near d = 0:
+// there its Taylor series sum_{k>=2} (-d)^k / (k (k - 1)), cut after d^9.
+__device__ __forceinline__ float kl_term(float d) {
+  if (fabsf(d) < 0.125f)
+    return d * d *
+           (0.5f + d * (-1.f / 6.f +
+                        d * (1.f / 12.f +
+                             d * (-1.f / 20.f +
+                                  d * (1.f / 30.f +
+                                       d * (-1.f / 42.f + d * (1.f / 56.f + d * (-1.f / 72.f))))))));
+  return (1.f + d) * log1pf(d) - d;
+}
+
 // ------------------------------------------------------------------ GLCM
 __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
                             int32_t* dbg_glcm) {
@@ -688,13 +701,21 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
   Magic mm;
   mm.init((unsigned)m);
   const int mm2 = m * m;
+  // merged aggregation: the 13 directions' pairs go into one matrix, whose
+  // features (and MCC, in slot 0) are taken once
+  const bool merged = job.agg == 1;
+  if (merged && want_mcc && lane < kNumDirs) {
+    mn[lane] = 0;
+    mres[lane] = kNaNf;
+  }
   acc_reset(A);
+  int np = 0;
   for (int di = 0; di < kNumDirs; ++di) {
     const int ddz = c_dirs[di][0] * job.delta, ddy = c_dirs[di][1] * job.delta,
               ddx = c_dirs[di][2] * job.delta;
     const int off = ddz * w.s2 + ddy * w.s + ddx;
     // pairs -> upper-triangle counts over compact indices (equal keys merged)
-    int np = 0;
+    if (!merged) np = 0;
     for (int base = 0; base < w.W; base += 32) {
       const int p = base + lane;
       int key = -1;
@@ -717,10 +738,12 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
       np += __popc(act);
     }
     __syncwarp();
+    if (merged && di < kNumDirs - 1) continue;
+    const int ds = merged ? 0 : di;  // slot / record of this matrix
     if (np == 0) {
       if (lane == 0) {
-        mn[di] = 0;
-        mres[di] = kNaNf;
+        mn[ds] = 0;
+        mres[ds] = kNaNf;
       }
       acc_lane(A, 23, kNaNf);
       continue;
@@ -728,7 +751,10 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
     const int T = 2 * np;
     const float fT = (float)T;
     // marginals (lane a sums row a of the symmetric matrix) and present list
-    unsigned m1 = 0, m2 = 0;
+    // 64-bit where a merged matrix (13 directions, up to 13 x 3375 pairs)
+    // can pass 2^32
+    unsigned m1 = 0;
+    unsigned long long m2 = 0;
     float hx = 0.f;
     int present = 0;
     for (int a0 = 0; a0 < m; a0 += 32) {
@@ -741,7 +767,7 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
         if (c) {
           const unsigned i = A.lev[a];
           m1 += i * (unsigned)c;
-          m2 += i * i * (unsigned)c;
+          m2 += (unsigned long long)(i * i) * (unsigned)c;
           hx += ent_term(c, T);
         }
       }
@@ -750,22 +776,27 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
       present += __popc(pb);
     }
     m1 = redux_u32(m1);
-    m2 = redux_u32(m2);
+    m2 = warp_sum_u64(m2);
     // MCC matrix of up to kCapL present levels: written by the entries pass
     // into this direction's slot (zero first: the padding beyond them)
     const bool slot = want_mcc && present >= 2 && present <= kCapL;
     // counts are cleared as the entries pass reads them, unless the
     // many-level MCC solve still needs them
     const bool clear_now = !want_mcc || present <= kCapL;
-    float* P = slots + di * kSlot;
+    float* P = slots + ds * kSlot;
     const float invT = __fdividef(1.f, fT);
     if (slot)
       for (int t = lane; t < kSlot; t += 32) P[t] = 0.f;
     __syncwarp();
     // entries: linear sums, entropies, mutual information, sum / difference
     // bins, the MCC slot
-    unsigned a1 = 0, e2 = 0, maxc = 0;
+    unsigned long long a1 = 0, e2 = 0, mi0 = 0;
+    unsigned maxc = 0;
+    // MI = sum over all level pairs of p ln(p/q) - p + q (q = p_a p_b; the
+    // extra terms sum to zero), every term >= 0: q g(p/q) where p > 0, and
+    // q where p = 0 (its sum kept exact in mi0 T^2); nats until the end
     float hxy = 0.f, mi = 0.f;
+    const float fT2 = fT * fT;
     for (int t0 = 0; t0 < mm2; t0 += 32) {
       const int t = t0 + lane;
       if (t >= mm2) continue;
@@ -773,27 +804,30 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
       if (b < a) continue;
       const int n = cnt[a * mc + b];
       if (!n) {
-        // S - u u^T is dense: an empty pair of present levels is -u_a u_b
-        if (slot) {
-          const int ca = marg[a], cb = marg[b];
-          if (ca && cb)
+        const int ca = marg[a], cb = marg[b];
+        if (ca && cb) {
+          // an empty pair of present levels: its q = p_a p_b enters MI, and
+          // S - u u^T is dense there (-u_a u_b)
+          const long long cc = (long long)ca * cb;
+          mi0 += (a == b ? 1ull : 2ull) * (unsigned long long)cc;
+          if (slot)
             P[pk(kCapL, prank[a], prank[b])] =
-                (float)(-(long long)ca * cb) * rsqrtf((float)ca * (float)cb) * invT;
+                (float)(-cc) * rsqrtf((float)ca * (float)cb) * invT;
         }
         continue;
       }
       const unsigned i = A.lev[a], j = A.lev[b];
       const int C = (a == b) ? 2 * n : n;
       const unsigned mult = (a == b) ? 1u : 2u;
-      a1 += mult * (unsigned)C * i * j;
-      e2 += mult * (unsigned)(C * C);
+      a1 += (unsigned long long)(mult * (unsigned)C) * (i * j);
+      e2 += (unsigned long long)(mult * (unsigned)C) * (unsigned)C;
       maxc = max(maxc, (unsigned)C);
       const float fm = (float)mult;
       hxy += fm * ent_term(C, T);
       const int ca = marg[a], cb = marg[b];
       const long long ct = (long long)C * T, cc = (long long)ca * cb;
       if (ct != cc)  // p = p_x p_y exactly contributes nothing
-        mi += fm * __fdividef((float)C, fT) * log2f(__fdividef((float)ct, (float)cc));
+        mi += fm * __fdividef((float)cc, fT2) * kl_term(__fdividef((float)(ct - cc), (float)cc));
       if (clear_now) cnt[a * mc + b] = 0;
       // A(a', b') = (C T - c_a c_b) / (T sqrt(c_a c_b)) over present ranks
       if (slot)
@@ -802,13 +836,14 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
       atomicAdd(&sbin[i + j - 2 * w.lev0], 2 * n);
       atomicAdd(&dbin[j - i], 2 * n);
       if (dbg_glcm) {
-        int32_t* g = dbg_glcm + (size_t)di * w.ng * w.ng;
+        int32_t* g = dbg_glcm + (size_t)ds * w.ng * w.ng;
         g[(i - 1) * w.ng + (j - 1)] = C;
         g[(j - 1) * w.ng + (i - 1)] = C;
       }
     }
-    a1 = redux_u32(a1);
-    e2 = redux_u32(e2);
+    a1 = warp_sum_u64(a1);
+    e2 = warp_sum_u64(e2);
+    mi0 = warp_sum_u64(mi0);
     maxc = __reduce_max_sync(kFull, maxc);
     __syncwarp();
     // MCC: the deflated A = S - u u^T, S = D^-1/2 P D^-1/2 over present levels
@@ -816,11 +851,11 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
       const int nd = present;
       if (nd < 2) {
         if (lane == 0) {
-          mn[di] = 0;
-          mres[di] = kNaNf;
+          mn[ds] = 0;
+          mres[ds] = kNaNf;
         }
       } else if (slot) {
-        if (lane == 0) mn[di] = nd;  // solved after the 13 directions
+        if (lane == 0) mn[ds] = nd;  // solved after the 13 directions
       } else {
         // many levels: warp-cooperative solve now, on S in place of the counts
         float* S = (float*)cnt;
@@ -841,8 +876,8 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
         __syncwarp();
         const float rho = spectral_radius(S, m, mc, vv, ww, dd, ee);
         if (lane == 0) {
-          mn[di] = 0;
-          mres[di] = rho;
+          mn[ds] = 0;
+          mres[ds] = rho;
         }
         __syncwarp();
         for (int t = lane; t < mm2; t += 32) {
@@ -854,7 +889,8 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
     __syncwarp();
     for (int a = lane; a < m; a += 32) marg[a] = 0;
     // difference and sum distributions (bins relative to the smallest level)
-    unsigned dk = 0, dk2 = 0, sk = 0;
+    unsigned dk = 0, sk = 0;
+    unsigned long long dk2 = 0;
     float de = 0.f, idm = 0.f, idmn = 0.f, idd = 0.f, idn = 0.f, iv = 0.f, se = 0.f,
           ce2 = 0.f, ce4 = 0.f;
     __int128 ce3 = 0;
@@ -866,7 +902,7 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
           dbin[k] = 0;
           const float fk = (float)k, fc = (float)c;
           dk += (unsigned)(k * c);
-          dk2 += (unsigned)(k * k * c);
+          dk2 += (unsigned long long)(k * k) * (unsigned)c;
           de += ent_term(c, T);
           idm += __fdividef(fc, 1.f + fk * fk);
           idmn += __fdividef(fc, 1.f + __fdividef(fk * fk, ngf * ngf));
@@ -881,32 +917,34 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
         const int kk = k + 2 * w.lev0;
         sk += (unsigned)(kk * c);
         se += ent_term(c, T);
-        const int e = T * kk - 2 * (int)m1;  // T (k - 2 mu), |e| < 2^24
+        // T (k - 2 mu): |e| < 2^24 per direction, < 2^26 merged
+        const int e = T * kk - 2 * (int)m1;
         const float fe = (float)e, fe2 = fe * fe;
         ce2 += (float)c * fe2;
         ce4 += (float)c * fe2 * fe2;
-        ce3 += (__int128)((long long)e * e * c) * e;
+        ce3 += (__int128)((long long)e * e) * ((long long)c * e);
       }
     }
     dk = redux_u32(dk);
-    dk2 = redux_u32(dk2);
+    dk2 = warp_sum_u64(dk2);
     sk = redux_u32(sk);
     ce3 = warp_sum_i128(ce3);
     float fs[12] = {hx, hxy, mi, de, idm, idmn, idd, idn, iv, se, ce2, ce4};
     warp_sum_f32x<12>(fs);
+    fs[2] = (fs[2] + __fdividef((float)mi0, fT2)) * 1.44269504088896341f;  // bits
     // one lane per feature
     float num = kNaNf, den = 1.f;
-    const long long var_num = (long long)T * m2 - (long long)m1 * m1;  // T^2 sigma^2
+    const long long var_num = (long long)T * (long long)m2 - (long long)m1 * m1;  // T^2 sigma^2
     if (lane == 0) { num = (float)a1; den = fT; }
     if (lane == 1) { num = (float)m1; den = fT; }
     if (lane == 2) { num = fs[11]; den = fT * fT * fT * fT * fT; }
     if (lane == 3) { num = i128_to_f32(ce3); den = fT * fT * fT * fT; }
     if (lane == 4) { num = fs[10]; den = fT * fT * fT; }
     if (lane == 5) { num = (float)dk2; den = fT; }
-    if (lane == 6) { num = (float)((long long)T * a1 - (long long)m1 * m1); den = (float)var_num; }
+    if (lane == 6) { num = (float)((long long)T * (long long)a1 - (long long)m1 * m1); den = (float)var_num; }
     if (lane == 7) { num = (float)dk; den = fT; }
     if (lane == 8) { num = fs[3]; }
-    if (lane == 9) { num = (float)((long long)T * dk2 - (long long)dk * dk); den = fT * fT; }
+    if (lane == 9) { num = (float)((long long)T * (long long)dk2 - (long long)dk * dk); den = fT * fT; }
     if (lane == 10) { num = (float)e2; den = fT * fT; }
     if (lane == 11) { num = fs[1]; }
     if (lane == 12) { num = -fs[2]; den = fs[0]; }
@@ -951,17 +989,21 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
 }
 
 // ------------------------------------------------------------------ GLRLM
-__device__ void glrlm_family(const Win& w, const Arena& A, int32_t* dbg_glrlm) {
+// merged: the 13 directions' runs go into one matrix, whose features are
+// taken once (RunPercentage over 13 N_v: each voxel lies on one run per
+// direction).
+__device__ void glrlm_family(const Win& w, const Arena& A, bool merged, int32_t* dbg_glrlm) {
   const int lane = lane_id();
   const int m = w.m;
   int* hist = (int*)(A.big + A.L.rhist);  // [mc][16]
   int* lnc = (int*)(A.big + A.L.rlen);    // column sums when m > 32
   acc_reset(A);
-  const float nvf = (float)w.nv;
+  const float nvf = merged ? (float)(kNumDirs * w.nv) : (float)w.nv;
+  int nr = 0;
   for (int di = 0; di < kNumDirs; ++di) {
     const int dz = c_dirs[di][0], dy = c_dirs[di][1], dx = c_dirs[di][2];
     const int off = dz * w.s2 + dy * w.s + dx;
-    int nr = 0;
+    if (!merged) nr = 0;
     for (int base = 0; base < w.W; base += 32) {
       const int p = base + lane;
       int key = -1;
@@ -991,6 +1033,8 @@ __device__ void glrlm_family(const Win& w, const Arena& A, int32_t* dbg_glrlm) {
       nr += __popc(act);
     }
     __syncwarp();
+    if (merged && di < kNumDirs - 1) continue;
+    const int ds = merged ? 0 : di;  // record of this matrix
     // row walk: lane a owns gray level a; columns are run lengths
     unsigned si = 0, si2 = 0, sj = 0, sj2 = 0, glnu = 0, rlnu = 0;
     float fs[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sre lgl srl srh lrl lrh ent
@@ -1023,7 +1067,7 @@ __device__ void glrlm_family(const Win& w, const Arena& A, int32_t* dbg_glrlm) {
           fs[4] += fc * fj2 * inv_i2;
           fs[5] += fc * fi2 * fj2;
           fs[6] += ent_term(c, nr);
-          if (dbg_glrlm) dbg_glrlm[((size_t)di * w.ng + (i - 1)) * w.s + jl] = c;
+          if (dbg_glrlm) dbg_glrlm[((size_t)ds * w.ng + (i - 1)) * w.s + jl] = c;
         }
       }
       glnu += row * row;

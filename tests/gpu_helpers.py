@@ -6,10 +6,12 @@ from oracle import oracle as O
 
 
 def oracle_params(shape, disc_mode=0, bin_count=16, bin_width=25.0, fbw_anchor=0,
-                  kernel_radius=1, glcm_distance=1, spacing=(1.0, 1.0, 1.0), kurtosis_excess=1):
+                  kernel_radius=1, glcm_distance=1, spacing=(1.0, 1.0, 1.0), kurtosis_excess=1,
+                  aggregation=0):
     return O.make_params(shape, disc_mode=disc_mode, bin_count=bin_count, bin_width=bin_width,
                          fbw_anchor=fbw_anchor, radius=kernel_radius, distance=glcm_distance,
-                         spacing=spacing, kurtosis_excess=kurtosis_excess)
+                         spacing=spacing, kurtosis_excess=kurtosis_excess,
+                         aggregation=aggregation)
 
 
 def gpu_map(img, mask, features=None, tune=None, **kw):

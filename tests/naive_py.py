@@ -305,15 +305,20 @@ def _nanmean_rows(a):
     return out
 
 
-def features_of_cube(lv, raw, ng, delta=1, vvox=1.0, excess=True):
-    """All 93 features of one sub-VOI cube."""
+def features_of_cube(lv, raw, ng, delta=1, vvox=1.0, excess=True, merged=False):
+    """All 93 features of one sub-VOI cube.  merged: GLCM and GLRLM features
+    of the sum of the 13 directional matrices (run percentage over 13 N_v)."""
     inside = lv > 0
     nv = int(inside.sum())
     fo = firstorder_features(raw[inside], lv[inside], ng, vvox, excess)
     G = glcm(lv, ng, delta)
-    gl = _nanmean_rows([glcm_features(G[k], ng) for k in range(13)])
     R = glrlm(lv, ng)
-    rl = _nanmean_rows([rl_features(R[k], nv) for k in range(13)])
+    if merged:
+        gl = glcm_features(G.sum(axis=0), ng)
+        rl = rl_features(R.sum(axis=0), 13 * nv)
+    else:
+        gl = _nanmean_rows([glcm_features(G[k], ng) for k in range(13)])
+        rl = _nanmean_rows([rl_features(R[k], nv) for k in range(13)])
     sz = rl_features(glszm(lv, ng), nv)
     dm = gldm_features(gldm(lv, ng))
     n, s = ngtdm_exact(lv, ng)
@@ -321,11 +326,11 @@ def features_of_cube(lv, raw, ng, delta=1, vvox=1.0, excess=True):
     return np.concatenate([fo, gl, rl, sz, dm, nt])
 
 
-def map_voxels(levels, image, ng, voxels, r, delta=1, vvox=1.0, excess=True):
+def map_voxels(levels, image, ng, voxels, r, delta=1, vvox=1.0, excess=True, merged=False):
     Z, Y, X = levels.shape
     out = []
     for lin in voxels:
         z, y, x = lin // (Y * X), (lin // X) % Y, lin % X
         lv, raw = sub_voi(levels, image, (z, y, x), r)
-        out.append(features_of_cube(lv, raw, ng, delta, vvox, excess))
+        out.append(features_of_cube(lv, raw, ng, delta, vvox, excess, merged))
     return np.array(out).T

@@ -78,7 +78,7 @@ def test_invalid_arguments_are_rejected_without_a_device():
     mask = (C.c_uint8 * 8)(*([1] * 8))
     for field, value in [("kernel_radius", 0), ("kernel_radius", 8), ("bin_count", 0),
                          ("bin_count", 256), ("glcm_distance", 0), ("nx", 0),
-                         ("disc_mode", 5), ("reserved", 1)]:
+                         ("disc_mode", 5), ("aggregation", 2)]:
         p = fm.fr_map_params_init(2, 2, 2)
         setattr(p, field, value)
         assert L.fr_map_plan(C.byref(p), mask, None, C.byref(h)) == 1, field

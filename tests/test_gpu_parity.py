@@ -62,6 +62,18 @@ def test_ct_crop_all_93_fbw(r):
     _check(img, mask, disc_mode=1, bin_width=25.0, kernel_radius=r)
 
 
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_ct_crop_all_93_merged_aggregation(r):
+    # GLCM and GLRLM over the sum of the 13 directional matrices
+    img, mask = _crop_ct(seed=6, shape=(16, 28, 32), semi=(14.0, 12.0, 7.0))
+    _check(img, mask, disc_mode=1, bin_width=25.0, kernel_radius=r, aggregation=1)
+
+
+def test_tiny_merged_aggregation_fbn16():
+    img, mask = synth.tiny(seed=1)
+    _check(img, mask, disc_mode=0, bin_count=16, kernel_radius=1, aggregation=1)
+
+
 def test_ct_crop_fbn64_r3_slab_path():
     # FBN 64 makes windows with more than 32 levels or a level range >= 64
     # possible; the kernel then uses its global slab.
