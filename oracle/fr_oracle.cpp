@@ -142,6 +142,24 @@ Cube make_cube(const fro_params* p, const int16_t* img, const uint8_t* levels,
   return c;
 }
 
+/* The whole volume as one cube of side max(nx, ny, nz) (zeros beyond it):
+ * the sub-VOI of a window that covers every VOI voxel. */
+Cube make_whole_cube(const fro_params* p, const int16_t* img, const uint8_t* levels) {
+  Cube c;
+  c.s = std::max(p->nx, std::max(p->ny, p->nz));
+  c.lev.assign((size_t)c.s * c.s * c.s, 0);
+  c.raw.assign((size_t)c.s * c.s * c.s, 0);
+  for (int z = 0; z < p->nz; ++z)
+    for (int y = 0; y < p->ny; ++y)
+      for (int x = 0; x < p->nx; ++x) {
+        const int64_t lin = ((int64_t)z * p->ny + y) * p->nx + x;
+        if (!levels[lin]) continue;
+        c.lev[c.at(z, y, x)] = levels[lin];
+        c.raw[c.at(z, y, x)] = img[lin];
+      }
+  return c;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Matrices                                                                 */
 /* ---------------------------------------------------------------------- */
@@ -210,6 +228,48 @@ void glszm_counts(const Cube& c, int ng, std::vector<double>& Z) {
           }
     }
     Z[(size_t)(a - 1) * w + (queue.size() - 1)] += 1.0;
+  }
+}
+
+/* The same zones as counts per (level, size) over only the sizes that occur:
+ * Z[ng][jv.size()], column k holding zones of size jv[k] (ascending).  Zone
+ * sizes reach N_v, so a dense size axis does not fit whole-VOI cubes. */
+void glszm_zones(const Cube& c, int ng, std::vector<double>& Z, std::vector<double>& jv) {
+  const int w = c.s * c.s * c.s;
+  std::vector<char> seen(w, 0);
+  std::vector<int> queue;
+  std::vector<std::pair<int, int>> zones;  // (level, size)
+  for (int start = 0; start < w; ++start) {
+    if (!c.lev[start] || seen[start]) continue;
+    const int a = c.lev[start];
+    queue.clear();
+    queue.push_back(start);
+    seen[start] = 1;
+    for (size_t head = 0; head < queue.size(); ++head) {
+      int k = queue[head];
+      int z = k / (c.s * c.s), y = (k / c.s) % c.s, x = k % c.s;
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (!dz && !dy && !dx) continue;
+            if (!c.inside(z + dz, y + dy, x + dx)) continue;
+            int q = c.at(z + dz, y + dy, x + dx);
+            if (seen[q] || c.lev[q] != a) continue;
+            seen[q] = 1;
+            queue.push_back(q);
+          }
+    }
+    zones.push_back({a, (int)queue.size()});
+  }
+  std::vector<int> sizes;
+  for (auto& z : zones) sizes.push_back(z.second);
+  std::sort(sizes.begin(), sizes.end());
+  sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+  jv.assign(sizes.begin(), sizes.end());
+  Z.assign((size_t)ng * sizes.size(), 0.0);
+  for (auto& z : zones) {
+    const size_t col = std::lower_bound(sizes.begin(), sizes.end(), z.second) - sizes.begin();
+    Z[(size_t)(z.first - 1) * sizes.size() + col] += 1.0;
   }
 }
 
@@ -451,8 +511,11 @@ void glcm_features(const std::vector<double>& C, int ng, double* f) {
  * (1..ng) and j = column + 1 the run length, zone size or dependence.  The
  * 16 GLRLM and the 16 GLSZM features share these formulas; nv is the number
  * of voxels (the denominator of run/zone percentage). */
-void rl_features(const std::vector<double>& R, int ng, int nj, double nv,
-                 double* f) {
+/* Run-length / size-zone features of R[ng][nj] whose column j counts runs
+ * (zones) of length (size) jv[j]. */
+void rl_features_j(const std::vector<double>& R, int ng, const std::vector<double>& jv,
+                   double nv, double* f) {
+  const int nj = (int)jv.size();
   double N = 0;
   for (double v : R) N += v;
   if (N == 0) {
@@ -470,7 +533,7 @@ void rl_features(const std::vector<double>& R, int ng, int nj, double nv,
     for (int j = 0; j < nj; ++j) {
       double p = R[(size_t)i * nj + j] / N;
       mui += (i + 1) * p;
-      muj += (j + 1) * p;
+      muj += jv[j] * p;
     }
   double sre = 0, lre = 0, glv = 0, rv = 0, ent = 0, lgl = 0, hgl = 0, srl = 0,
          srh = 0, lrl = 0, lrh = 0;
@@ -478,7 +541,7 @@ void rl_features(const std::vector<double>& R, int ng, int nj, double nv,
     for (int j = 0; j < nj; ++j) {
       double p = R[(size_t)i * nj + j] / N;
       if (p == 0) continue;
-      double I = i + 1, J = j + 1;
+      double I = i + 1, J = jv[j];
       sre += p / (J * J);
       lre += p * J * J;
       glv += (I - mui) * (I - mui) * p;
@@ -510,6 +573,13 @@ void rl_features(const std::vector<double>& R, int ng, int nj, double nv,
   f[13] = srh;
   f[14] = lrl;
   f[15] = lrh;
+}
+
+/* The same with column j holding length (size) j + 1. */
+void rl_features(const std::vector<double>& R, int ng, int nj, double nv, double* f) {
+  std::vector<double> jv(nj);
+  for (int j = 0; j < nj; ++j) jv[j] = j + 1;
+  rl_features_j(R, ng, jv, nv, f);
 }
 
 /* GLDM features of a [ng][nj] dependence count matrix (j = column + 1). */
@@ -782,8 +852,9 @@ void map_one(const fro_params* p, const Cube& c, int ng, double* f) {
     average_dirs(per, FRO_NUM_DIRS, 16, f + 42);
   }
 
-  glszm_counts(c, ng, M);
-  rl_features(M, ng, c.s * c.s * c.s, nv, f + 58);
+  std::vector<double> jv;
+  glszm_zones(c, ng, M, jv);
+  rl_features_j(M, ng, jv, nv, f + 58);
 
   gldm_counts(c, ng, M);
   gldm_features(M, ng, 27, f + 74);
@@ -891,6 +962,21 @@ int32_t fro_map_voxels(const fro_params* p, const int16_t* img,
     for (int q = 0; q < FRO_NUM_FEATURES; ++q) out[(size_t)q * n + k] = f[q];
   }
   (void)nthreads;
+  return 0;
+}
+
+int32_t fro_scalar(const fro_params* p, const int16_t* img, const uint8_t* levels,
+                   int32_t ng, double* out) {
+  if (!p) return 3;
+  fro_params q = *p;
+  q.radius = 1;  /* the window is the whole volume; radius plays no part */
+  if (!params_ok(&q)) return 3;
+  bool any = false;
+  const int64_t nvox = (int64_t)p->nx * p->ny * p->nz;
+  for (int64_t k = 0; k < nvox && !any; ++k) any = levels[k] != 0;
+  if (!any) return 1;
+  Cube c = make_whole_cube(p, img, levels);
+  map_one(&q, c, ng, out);
   return 0;
 }
 

@@ -78,6 +78,13 @@ int32_t fro_map_voxels(const fro_params* p, const int16_t* img,
                        const uint8_t* levels, int32_t ng, const int64_t* vox,
                        int64_t n, double* out, int32_t nthreads);
 
+/* Scalar extraction: the 93 features of the whole VOI (the paper's other
+ * extraction mode; the map value at v equals it whenever the window around v
+ * covers the VOI).  levels from fro_discretise; p->radius is ignored.
+ * Returns 0, 1 for an empty VOI, 3 for invalid parameters. */
+int32_t fro_scalar(const fro_params* p, const int16_t* img, const uint8_t* levels,
+                   int32_t ng, double* out93);
+
 /* Dense texture matrices of one voxel's sub-VOI V(v) (bit-exact integers).
  * glcm  : [13][ng][ng]  symmetric co-occurrence counts (levels 1..ng at 0..ng-1)
  * glrlm : [13][ng][s]   runs of level i and length j+1, s = 2r+1

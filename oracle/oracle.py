@@ -59,6 +59,7 @@ def lib():
         L.fro_map_voxels.argtypes = [P(Params), C.c_void_p, C.c_void_p, C.c_int32,
                                      C.c_void_p, C.c_int64, C.c_void_p, C.c_int32]
         L.fro_matrices.argtypes = [P(Params), C.c_void_p, C.c_int32, C.c_int64] + [C.c_void_p] * 7
+        L.fro_scalar.argtypes = [P(Params), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
         L.fro_glcm_features.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
         L.fro_glrlm_features.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p]
         L.fro_glszm_features.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p]
@@ -129,6 +130,17 @@ def map_volume(params, image, mask, nthreads=0):
     levels, ng, _, _ = discretise(params, image, mask)
     vox = np.flatnonzero(np.asarray(mask).reshape(-1)).astype(np.int64)
     return map_voxels(params, image, levels, ng, vox, nthreads), vox, levels, ng
+
+
+def scalar(params, image, levels, ng):
+    """The 93 features of the whole VOI (scalar extraction)."""
+    image = np.ascontiguousarray(image, dtype=np.int16)
+    levels = np.ascontiguousarray(levels, dtype=np.uint8)
+    out = np.empty(NUM_FEATURES)
+    rc = lib().fro_scalar(C.byref(params), _ptr(image), _ptr(levels), ng, _ptr(out))
+    if rc != 0:
+        raise OracleError("fro_scalar failed with code %d" % rc)
+    return out
 
 
 def matrices(params, levels, ng, voxel):

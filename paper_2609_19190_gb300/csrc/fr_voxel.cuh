@@ -776,7 +776,7 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
       present += __popc(pb);
     }
     m1 = redux_u32(m1);
-    m2 = warp_sum_u64(m2);
+    m2 = merged ? warp_sum_u64(m2) : redux_u32((unsigned)m2);  // < 2^32 per direction
     // MCC matrix of up to kCapL present levels: written by the entries pass
     // into this direction's slot (zero first: the padding beyond them)
     const bool slot = want_mcc && present >= 2 && present <= kCapL;
@@ -841,9 +841,15 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
         g[(j - 1) * w.ng + (i - 1)] = C;
       }
     }
-    a1 = warp_sum_u64(a1);
-    e2 = warp_sum_u64(e2);
-    mi0 = warp_sum_u64(mi0);
+    if (merged) {
+      a1 = warp_sum_u64(a1);
+      e2 = warp_sum_u64(e2);
+      mi0 = warp_sum_u64(mi0);
+    } else {  // one direction: each < 2^32
+      a1 = redux_u32((unsigned)a1);
+      e2 = redux_u32((unsigned)e2);
+      mi0 = redux_u32((unsigned)mi0);
+    }
     maxc = __reduce_max_sync(kFull, maxc);
     __syncwarp();
     // MCC: the deflated A = S - u u^T, S = D^-1/2 P D^-1/2 over present levels
@@ -926,7 +932,7 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
       }
     }
     dk = redux_u32(dk);
-    dk2 = warp_sum_u64(dk2);
+    dk2 = merged ? warp_sum_u64(dk2) : redux_u32((unsigned)dk2);
     sk = redux_u32(sk);
     ce3 = warp_sum_i128(ce3);
     float fs[12] = {hx, hxy, mi, de, idm, idmn, idd, idn, iv, se, ce2, ce4};

@@ -503,6 +503,39 @@ def test_merged_linear_features_are_weighted_direction_means():
     np.testing.assert_array_equal(mrg[58:], avg[58:])
 
 
+@pytest.mark.parametrize("kw", [dict(disc_mode=O.FBN, bin_count=6),
+                                dict(disc_mode=O.FBW, bin_width=30.0),
+                                dict(disc_mode=O.FBN, bin_count=5, aggregation=O.AGG_MERGED)])
+def test_scalar_against_naive_whole_cube(kw):
+    # scalar extraction = the features of the whole VOI, by brute force
+    rng = np.random.default_rng(50)
+    img = rng.integers(-100, 100, size=(9, 11, 10)).astype(np.int16)
+    mask = (rng.random(img.shape) < 0.6).astype(np.uint8)
+    p = O.make_params(img.shape, spacing=(0.7, 1.0, 1.5), **kw)
+    lev, ng, _, _ = O.discretise(p, img, mask)
+    got = O.scalar(p, img, lev, ng)
+    S = max(img.shape)
+    cube = np.zeros((S, S, S), np.int64)
+    raw = np.zeros((S, S, S), np.int64)
+    cube[:9, :11, :10] = lev
+    raw[:9, :11, :10] = img
+    ref = NP.features_of_cube(cube, raw, ng, vvox=0.7 * 1.0 * 1.5,
+                              merged=kw.get("aggregation", 0) == O.AGG_MERGED)
+    np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-9, equal_nan=True)
+
+
+def test_scalar_equals_every_map_value_when_windows_cover_the_voi():
+    rng = np.random.default_rng(51)
+    img = rng.integers(0, 500, size=(12, 12, 12)).astype(np.int16)
+    mask = np.zeros(img.shape, np.uint8)
+    mask[4:9, 3:8, 5:10] = rng.random((5, 5, 5)) < 0.7
+    kw = dict(disc_mode=O.FBN, bin_count=8, radius=5)
+    maps, vox, levels, ng = _oracle_maps(img, mask, **kw)
+    sc = O.scalar(O.make_params(img.shape, **kw), img, levels, ng)
+    for k in range(maps.shape[1]):
+        np.testing.assert_allclose(maps[:, k], sc, rtol=1e-12, atol=1e-12, equal_nan=True)
+
+
 def test_map_flip_permutation_translation_equivariance():
     rng = np.random.default_rng(31)
     img = rng.integers(0, 40, size=(7, 6, 5)).astype(np.int16)
