@@ -210,6 +210,32 @@ fr_status fr_batch_sync_status(fr_batch* b);
 fr_status fr_batch_last_kernel_ms(fr_batch* b, float* ms);
 void fr_batch_destroy(fr_batch* b);
 
+/* Scalar extraction (the paper's other extraction mode, "Software design and
+ * extraction modes"): the selected features of the whole VOI, one value per
+ * feature -- the map value of a window that covers every VOI voxel (so
+ * kernel_radius plays no part).  Same parameters, discretisation,
+ * aggregation and feature ids as mapping.  Counts are exact integers; the
+ * features are computed in FP64 (MCC in FP32).
+ *
+ * fr_scalar_plan: discretisation plan and whole-VOI count buffers (about
+ *   8 B per volume voxel + 12 B per VOI voxel + 13 x Ng x max(nx, ny, nz) x 4
+ *   B); synchronous; mask as for fr_map_plan.  Errors as fr_map_plan.
+ * fr_scalar_run: image_dev int16 [nz][ny][nx] on the plan's device; out_dev
+ *   double [n_features] (selected features in id order), caller-owned, on the
+ *   device.  Asynchronous on s; one run at a time per plan.  Device errors
+ *   (Ng > 255 for FBW) are reported by fr_scalar_sync_status, and the outputs
+ *   are then NaN.  Zone sums visit a hash table whose slot order can depend
+ *   on thread timing, so GLSZM values may differ in the last bits between
+ *   runs; everything else is deterministic. */
+typedef struct fr_scalar fr_scalar;
+fr_status fr_scalar_plan(const fr_map_params* p, const uint8_t* mask, fr_scalar** out);
+fr_status fr_scalar_run(fr_scalar* sp, const int16_t* image_dev, double* out_dev,
+                        fr_stream_t s);
+fr_status fr_scalar_sync_status(fr_scalar* sp);
+fr_status fr_scalar_query(const fr_scalar* sp, int64_t* n_voi, int32_t* n_features,
+                          size_t* device_bytes);
+void fr_scalar_destroy(fr_scalar* sp);
+
 /* Continuous-batching server (iteration-level scheduling).  Requests are
  * planned as they arrive (fr_server_add: synchronous, allocates the request's
  * device state; mask, image and out are device pointers that must stay valid

@@ -152,6 +152,64 @@ def fr_map_run_host(plan, image, out=None, stream=None):
     return out
 
 
+class ScalarPlan:
+    """Handle of an fr_scalar (whole-VOI scalar extraction)."""
+
+    def __init__(self, handle, params):
+        self.handle = handle
+        self.params = params
+        n_voi, nf, nbytes = C.c_int64(), C.c_int32(), C.c_size_t()
+        check("fr_scalar_query", _lib.load().fr_scalar_query(handle, C.byref(n_voi), C.byref(nf),
+                                                              C.byref(nbytes)))
+        self.n_voi, self.n_features, self.device_bytes = n_voi.value, nf.value, nbytes.value
+        self.features = selected_features(params)
+
+    def __del__(self):
+        try:
+            fr_scalar_destroy(self)
+        except Exception:
+            pass
+
+
+def fr_scalar_plan(params, mask):
+    """Plan a scalar extraction (mask as for fr_map_plan)."""
+    torch = _torch()
+    L = _lib.load()
+    if not isinstance(mask, torch.Tensor):
+        mask = torch.from_numpy(mask)
+    mask = mask.to(torch.uint8).contiguous()
+    params.mask_on_device = 1 if mask.is_cuda else 0
+    if mask.is_cuda:
+        params.device = mask.device.index or 0
+    h = C.c_void_p()
+    check("fr_scalar_plan", L.fr_scalar_plan(C.byref(params), C.c_void_p(mask.data_ptr()),
+                                             C.byref(h)))
+    return ScalarPlan(h, params)
+
+
+def fr_scalar_run(sp, image, out=None, stream=None):
+    """Features of the whole VOI of an int16 CUDA image [nz, ny, nx]; returns
+    out [n_features] float64 on the device."""
+    torch = _torch()
+    assert image.is_cuda and image.dtype == torch.int16 and image.is_contiguous()
+    if out is None:
+        out = torch.empty((sp.n_features,), dtype=torch.float64, device=image.device)
+    check("fr_scalar_run", _lib.load().fr_scalar_run(sp.handle, C.c_void_p(image.data_ptr()),
+                                                     C.c_void_p(out.data_ptr()),
+                                                     _stream_ptr(stream)))
+    return out
+
+
+def fr_scalar_sync_status(sp):
+    check("fr_scalar_sync_status", _lib.load().fr_scalar_sync_status(sp.handle))
+
+
+def fr_scalar_destroy(sp):
+    if getattr(sp, "handle", None):
+        _lib.load().fr_scalar_destroy(sp.handle)
+        sp.handle = None
+
+
 def fr_map_sync_status(plan):
     check("fr_map_sync_status", _lib.load().fr_map_sync_status(plan.handle))
 

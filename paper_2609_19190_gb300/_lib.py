@@ -67,6 +67,12 @@ SIGNATURES = {
     "fr_batch_run": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), _P]),
     "fr_batch_sync_status": (C.c_int, [_P]),
     "fr_batch_destroy": (None, [_P]),
+    "fr_scalar_plan": (C.c_int, [C.POINTER(MapParams), _P, C.POINTER(_P)]),
+    "fr_scalar_run": (C.c_int, [_P, _P, _P, _P]),
+    "fr_scalar_sync_status": (C.c_int, [_P]),
+    "fr_scalar_query": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_size_t)]),
+    "fr_scalar_destroy": (None, [_P]),
     "fr_voxel_list_noalloc": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int64,
                                         C.POINTER(C.c_int64), C.c_int32, _P]),
     "fr_server_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(Tune),

@@ -22,6 +22,10 @@ cudaError_t fr_map_configure(bool dump, int smem_bytes);
 cudaError_t fr_map_occupancy(bool dump, int threads, int smem_bytes, int* blocks);
 cudaError_t fr_map_launch(bool dump, const FrMapArgs& args, int grid, int smem_bytes,
                           cudaStream_t s);
+// fr_scalar.cu
+cudaError_t fr_scalar_configure(int ngc);
+cudaError_t fr_scalar_launch(const FrScalarArgs& a, double* user_out, const int16_t* row_of_dev,
+                             int sms, cudaStream_t s);
 // fr_prep.cu
 cudaError_t fr_launch_prepare(const FrJob* jobs, int njobs, int64_t max_voi,
                               void* const* run_ptrs, uint32_t* queue, int32_t* status,
@@ -725,6 +729,169 @@ struct fr_batch {
   Engine E;
 };
 
+// Scalar extraction: the discretised VOI (a planned job without bricks) and
+// the count buffers of the whole-VOI matrices, in one allocation.
+struct fr_scalar {
+  JobRes j;
+  int device = 0, sms = 0;
+  FrJob* d_job = nullptr;
+  void** d_run = nullptr;
+  uint32_t* d_queue = nullptr;
+  int32_t* d_status = nullptr;
+  int16_t* d_row_of = nullptr;
+  char* scratch = nullptr;
+  size_t zero_bytes = 0;  // counts at the start of scratch, cleared per run
+  size_t key_off = 0, key_bytes = 0;  // hash keys, set to ~0 per run
+  size_t bytes = 0;
+  FrScalarArgs A;
+  cudaEvent_t done = nullptr;
+  bool ran = false;
+
+  void release() {
+    j.release();
+    cudaFree(d_job);
+    cudaFree(d_run);
+    cudaFree(d_queue);
+    cudaFree(d_status);
+    cudaFree(d_row_of);
+    cudaFree(scratch);
+    if (done) cudaEventDestroy(done);
+    d_job = nullptr;
+    d_run = nullptr;
+    d_queue = nullptr;
+    d_status = nullptr;
+    d_row_of = nullptr;
+    scratch = nullptr;
+    done = nullptr;
+  }
+};
+
+namespace {
+
+fr_status scalar_open(fr_scalar& S, const fr_map_params* p, const uint8_t* mask) {
+  if (!valid_params(p) || !mask) return FR_ERR_INVALID_ARG;
+  S.device = p->device;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || S.device < 0 || S.device >= ndev)
+    return FR_ERR_UNSUPPORTED;
+  if (cudaSetDevice(S.device) != cudaSuccess) return FR_ERR_CUDA;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, S.device) != cudaSuccess) return FR_ERR_CUDA;
+  if (prop.major != 10 || prop.minor != 3) return FR_ERR_UNSUPPORTED;
+  S.sms = prop.multiProcessorCount;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return FR_ERR_CUDA;
+  fr_status st = build_job(p, mask, default_tune(nullptr), S.j, s);
+  if (st != FR_OK) {
+    cudaStreamDestroy(s);
+    return st;
+  }
+  try {
+    JobRes& j = S.j;
+    FrJob h;
+    memset((void*)&h, 0, sizeof(FrJob));
+    h.packed = j.packed;
+    h.voi = j.voi;
+    h.bcols = j.bcols;
+    h.state = j.state;
+    h.n_voi = j.n_voi;
+    h.nx = p->nx;
+    h.ny = p->ny;
+    h.nz = p->nz;
+    h.px = j.px;
+    h.r = p->kernel_radius;
+    h.delta = p->glcm_distance;
+    h.agg = p->aggregation;
+    h.disc_mode = p->disc_mode;
+    h.bin_count = p->bin_count;
+    h.anchor_zero_floor = p->fbw_anchor == FR_ANCHOR_ZERO_FLOOR;
+    h.kurt_excess = p->kurtosis_excess ? 1 : 0;
+    h.nf = j.nf;
+    h.families = j.families;
+    h.bin_width = p->bin_width;
+    h.voxel_volume = p->spacing[0] * p->spacing[1] * p->spacing[2];
+    memcpy(h.row_of, j.row_of, sizeof(h.row_of));
+    S.d_job = dev_alloc<FrJob>(1, &S.bytes);
+    FR_TRY(cudaMemcpyAsync(S.d_job, &h, sizeof(FrJob), cudaMemcpyHostToDevice, s));
+    S.d_run = dev_alloc<void*>(2, &S.bytes);
+    S.d_queue = dev_alloc<uint32_t>(1, &S.bytes);
+    S.d_status = dev_alloc<int32_t>(1, &S.bytes);
+    S.d_row_of = dev_alloc<int16_t>(96, &S.bytes);
+    FR_TRY(cudaMemcpyAsync(S.d_row_of, j.row_of, sizeof(j.row_of), cudaMemcpyHostToDevice, s));
+    // count buffers (cleared per run) first, then the rest
+    const int ngc = j.ngc;
+    const int64_t nvox = (int64_t)p->nx * p->ny * p->nz;
+    const int lmax = std::max(p->nx, std::max(p->ny, p->nz));
+    int64_t hcap = 1024;
+    while (hcap < 2 * j.n_voi) hcap <<= 1;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+      const size_t o = off;
+      off = (off + b + 255) / 256 * 256;
+      return o;
+    };
+    const size_t o_hraw = take(65536 * 4), o_hlev = take(256 * 4), o_gldm = take(256 * 27 * 4),
+                 o_ngn = take(256 * 4), o_ngacc = take(256 * 27 * 8),
+                 o_glcm = take((size_t)kNumDirs * (ngc * (ngc + 1) / 2) * 4),
+                 o_glrlm = take((size_t)kNumDirs * ngc * lmax * 4), o_zsize = take((size_t)nvox * 4),
+                 o_zrow = take(256 * 4), o_zcol = take((size_t)(j.n_voi + 1) * 4),
+                 o_hcnt = take((size_t)hcap * 4);
+    S.zero_bytes = off;
+    const size_t o_hkey = take((size_t)hcap * 8);
+    S.key_off = o_hkey;
+    S.key_bytes = (size_t)hcap * 8;
+    const size_t o_parent = take((size_t)nvox * 4),
+                 o_mccs = take((size_t)kNumDirs * ngc * ngc * 4),
+                 o_mccv = take((size_t)kNumDirs * 4 * ngc * 4), o_dirf = take(kNumDirs * 40 * 8),
+                 o_out = take(96 * 8);
+    S.scratch = dev_alloc<char>(off, &S.bytes);
+    FrScalarArgs& A = S.A;
+    memset((void*)&A, 0, sizeof(A));
+    A.packed = j.packed;
+    A.voi = j.voi;
+    A.state = j.state;
+    A.n_voi = j.n_voi;
+    A.nx = p->nx;
+    A.ny = p->ny;
+    A.nz = p->nz;
+    A.px = j.px;
+    A.ngc = ngc;
+    A.lmax = lmax;
+    A.delta = p->glcm_distance;
+    A.agg = p->aggregation;
+    A.kurt_excess = p->kurtosis_excess ? 1 : 0;
+    A.voxel_volume = h.voxel_volume;
+    A.hraw = (uint32_t*)(S.scratch + o_hraw);
+    A.hlev = (uint32_t*)(S.scratch + o_hlev);
+    A.gldm = (uint32_t*)(S.scratch + o_gldm);
+    A.ngn = (uint32_t*)(S.scratch + o_ngn);
+    A.ngacc = (unsigned long long*)(S.scratch + o_ngacc);
+    A.glcm = (uint32_t*)(S.scratch + o_glcm);
+    A.glrlm = (uint32_t*)(S.scratch + o_glrlm);
+    A.zsize = (int32_t*)(S.scratch + o_zsize);
+    A.zrow = (uint32_t*)(S.scratch + o_zrow);
+    A.zcol = (uint32_t*)(S.scratch + o_zcol);
+    A.hcnt = (uint32_t*)(S.scratch + o_hcnt);
+    A.hkey = (unsigned long long*)(S.scratch + o_hkey);
+    A.hcap = hcap;
+    A.parent = (int32_t*)(S.scratch + o_parent);
+    A.mcc_s = (float*)(S.scratch + o_mccs);
+    A.mcc_v = (float*)(S.scratch + o_mccv);
+    A.dirf = (double*)(S.scratch + o_dirf);
+    A.out = (double*)(S.scratch + o_out);
+    A.status = S.d_status;
+    FR_TRY(fr_scalar_configure(ngc));
+    FR_TRY(cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming));
+    FR_TRY(cudaStreamSynchronize(s));
+  } catch (CudaFail& f) {
+    st = f.st;
+  }
+  cudaStreamDestroy(s);
+  return st;
+}
+
+}  // namespace
+
 extern "C" {
 
 void fr_map_params_init(fr_map_params* p, int32_t nx, int32_t ny, int32_t nz) {
@@ -1350,6 +1517,71 @@ fr_status fr_direction(int32_t i, int32_t* dz, int32_t* dy, int32_t* dx) {
   *dy = kDirs[i][1];
   *dx = kDirs[i][2];
   return FR_OK;
+}
+
+fr_status fr_scalar_plan(const fr_map_params* p, const uint8_t* mask, fr_scalar** out) {
+  if (!out) return FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!p || !mask) return FR_ERR_INVALID_ARG;
+  fr_scalar* S = new (std::nothrow) fr_scalar();
+  if (!S) return FR_ERR_OOM;
+  fr_status st = scalar_open(*S, p, mask);
+  if (st != FR_OK) {
+    S->release();
+    delete S;
+    return st;
+  }
+  *out = S;
+  return FR_OK;
+}
+
+fr_status fr_scalar_run(fr_scalar* S, const int16_t* image, double* out, fr_stream_t stream) {
+  if (!S || !image || !out) return FR_ERR_INVALID_ARG;
+  if (cudaSetDevice(S->device) != cudaSuccess) return FR_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  void* ptrs[2] = {(void*)image, (void*)out};
+  if (cudaMemcpyAsync(S->d_run, ptrs, sizeof(ptrs), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return FR_ERR_CUDA;
+  if (fr_launch_prepare(S->d_job, 1, S->j.n_voi, S->d_run, S->d_queue, S->d_status, S->sms, s) !=
+      cudaSuccess)
+    return FR_ERR_CUDA;
+  if (cudaMemsetAsync(S->scratch, 0, S->zero_bytes, s) != cudaSuccess ||
+      cudaMemsetAsync(S->scratch + S->key_off, 0xFF, S->key_bytes, s) != cudaSuccess)
+    return FR_ERR_CUDA;
+  if (fr_scalar_launch(S->A, out, S->d_row_of, S->sms, s) != cudaSuccess) return FR_ERR_CUDA;
+  if (cudaEventRecord(S->done, s) != cudaSuccess) return FR_ERR_CUDA;
+  S->ran = true;
+  return FR_OK;
+}
+
+fr_status fr_scalar_sync_status(fr_scalar* S) {
+  if (!S) return FR_ERR_INVALID_ARG;
+  if (cudaSetDevice(S->device) != cudaSuccess) return FR_ERR_CUDA;
+  if (S->ran && cudaEventSynchronize(S->done) != cudaSuccess) return FR_ERR_CUDA;
+  int32_t st = 0;
+  if (cudaMemcpy(&st, S->d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FR_ERR_CUDA;
+  if (st) return (fr_status)st;
+  FrJobState js;
+  if (cudaMemcpy(&js, S->j.state, sizeof(js), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FR_ERR_CUDA;
+  return (fr_status)js.status;
+}
+
+fr_status fr_scalar_query(const fr_scalar* S, int64_t* n_voi, int32_t* n_features,
+                          size_t* device_bytes) {
+  if (!S) return FR_ERR_INVALID_ARG;
+  if (n_voi) *n_voi = S->j.n_voi;
+  if (n_features) *n_features = S->j.nf;
+  if (device_bytes) *device_bytes = S->bytes + S->j.bytes;
+  return FR_OK;
+}
+
+void fr_scalar_destroy(fr_scalar* S) {
+  if (!S) return;
+  cudaSetDevice(S->device);
+  S->release();
+  delete S;
 }
 
 }  // extern "C"

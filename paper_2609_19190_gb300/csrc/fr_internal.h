@@ -107,6 +107,39 @@ struct FrMapArgs {
   int64_t timeout_ns;  // bound of every device wait
 };
 
+// Scalar extraction (the whole VOI as one region): device buffers and sizes.
+// Counts are exact integers; features are taken in FP64 (MCC in FP32).
+struct FrScalarArgs {
+  const uint32_t* packed;      // ((raw + 32768) << 8) | level, 0 outside the VOI
+  const int32_t* voi;          // linear index of each VOI voxel
+  const FrJobState* state;     // xmin, xmax, ng, status of the discretisation
+  int64_t n_voi;
+  int32_t nx, ny, nz, px;
+  int32_t ngc;                 // level cap of the count buffers (<= 255)
+  int32_t lmax;                // longest possible run: max(nx, ny, nz)
+  int32_t delta, agg, kurt_excess;
+  double voxel_volume;
+  uint32_t* hraw;              // [65536] raw-intensity histogram
+  uint32_t* hlev;              // [256] level histogram
+  uint32_t* gldm;              // [256][27] dependence counts
+  uint32_t* ngn;               // [256] NGTDM n_i
+  unsigned long long* ngacc;   // [256][27] sum |i k - sum of neighbours| by k
+  uint32_t* glcm;              // [13][ngc (ngc + 1) / 2] packed upper-triangle pair counts
+  uint32_t* glrlm;             // [13][ngc][lmax] run counts
+  int32_t* parent;             // [nvox] union-find forest over VOI voxels
+  int32_t* zsize;              // [nvox] zone size at each root
+  uint32_t* zrow;              // [256] zones per level
+  uint32_t* zcol;              // [n_voi + 1] zones per size
+  unsigned long long* hkey;    // [hcap] (level << 32 | size) keys, ~0 = empty
+  uint32_t* hcnt;              // [hcap] zones per key
+  int64_t hcap;                // power of two >= 2 n_voi
+  float* mcc_s;                // [13][ngc][ngc] deflated S matrices
+  float* mcc_v;                // [13][4][ngc] solver vectors
+  double* dirf;                // [13][40] per-direction GLCM (24) + GLRLM (16)
+  double* out;                 // [93] feature values (written by the final kernel)
+  int32_t* status;             // run status word
+};
+
 // Big-region layout for caps (mc, bc) and window size w.
 struct BigLayout {
   int32_t cnt, marg, prank, sbin, dbin, vec;  // GLCM (vec: 4 float vectors of mc)

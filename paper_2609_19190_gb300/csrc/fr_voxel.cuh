@@ -151,7 +151,7 @@ __device__ __forceinline__ float lane_quot(float num, float den) {
 // ------------------------------------------------------------------ sorting
 // Ascending sort of n keys in a[0..n), padded to P = next power of two with
 // 0xffffffff.  Warp-synchronous bitonic network (registers for P <= 32).
-__device__ void warp_sort(uint32_t* a, int n) {
+static __device__ void warp_sort(uint32_t* a, int n) {
   const int lane = lane_id();
   int P = 1;
   while (P < n) P <<= 1;
@@ -214,7 +214,7 @@ __device__ __forceinline__ float ent_term(int c, int n) {
 // Copy the window of the voxel at tile offset (cx, cy, cz) (window corner)
 // from the staged halo tile: kb[0..nv) receives the packed words of V(v)
 // (compacted), lvl[p] the gray level (0 outside V(v)).
-__device__ int gather_window(const Win& w, const Arena& A, const uint32_t* tile,
+static __device__ int gather_window(const Win& w, const Arena& A, const uint32_t* tile,
                              int TX, int TY, int cx, int cy, int cz) {
   const int lane = lane_id();
   int nv = 0;
@@ -238,7 +238,7 @@ __device__ int gather_window(const Win& w, const Arena& A, const uint32_t* tile,
 // ------------------------------------------------------------------ first order
 // Sorted keys -> the 18 first-order features, the present-level table
 // (lev, lut), m, lev0, R and the level-count square sum.
-__device__ void first_order(Win& w, const Arena& A, const FrJob& job,
+static __device__ void first_order(Win& w, const Arena& A, const FrJob& job,
                             int32_t* dbg_hist) {
   const int lane = lane_id();
   const int N = w.nv;
@@ -368,7 +368,7 @@ __device__ void first_order(Win& w, const Arena& A, const FrJob& job,
 }
 
 // lvl[p]: level -> compact index + 1 (0 stays 0)
-__device__ void compact_levels(const Win& w, const Arena& A) {
+static __device__ void compact_levels(const Win& w, const Arena& A) {
   for (int p = lane_id(); p < w.W; p += 32) {
     int g = A.lvl[p];
     if (g) A.lvl[p] = (uint8_t)(A.lut[g] + 1);
@@ -421,7 +421,7 @@ __device__ __forceinline__ int sturm_below(const float* dd, const float* ee, int
 // Householder tridiagonalisation (warp-cooperative, A overwritten), then
 // Sturm-sequence multisection over 32 shifts per round.  Used for
 // directions with more than kCapL present levels.
-__device__ float spectral_radius(float* A, int n, int mc, float* vv, float* ww,
+static __device__ float spectral_radius(float* A, int n, int mc, float* vv, float* ww,
                                  float* dd, float* ee) {
   const int lane = lane_id();
   for (int k = 0; k + 2 < n; ++k) {
@@ -680,7 +680,7 @@ __device__ __forceinline__ float kl_term(float d) {
 }
 
 // ------------------------------------------------------------------ GLCM
-__device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
+static __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
                             int32_t* dbg_glcm) {
   const int lane = lane_id();
   const int m = w.m, mc = A.mc;
@@ -998,7 +998,7 @@ __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
 // merged: the 13 directions' runs go into one matrix, whose features are
 // taken once (RunPercentage over 13 N_v: each voxel lies on one run per
 // direction).
-__device__ void glrlm_family(const Win& w, const Arena& A, bool merged, int32_t* dbg_glrlm) {
+static __device__ void glrlm_family(const Win& w, const Arena& A, bool merged, int32_t* dbg_glrlm) {
   const int lane = lane_id();
   const int m = w.m;
   int* hist = (int*)(A.big + A.L.rhist);  // [mc][16]
@@ -1146,7 +1146,7 @@ __device__ __forceinline__ void uf_unite(int* parent, int a, int b) {
   }
 }
 
-__device__ void glszm_family(const Win& w, const Arena& A, int32_t* dbg_glszm) {
+static __device__ void glszm_family(const Win& w, const Arena& A, int32_t* dbg_glszm) {
   const int lane = lane_id();
   const int m = w.m;
   int* parent = (int*)(A.big + A.L.parent);
@@ -1264,7 +1264,7 @@ __device__ void glszm_family(const Win& w, const Arena& A, int32_t* dbg_glszm) {
 }
 
 // ------------------------------------------------------------------ GLDM + NGTDM
-__device__ void gldm_ngtdm_family(const Win& w, const Arena& A, const FrJob& job,
+static __device__ void gldm_ngtdm_family(const Win& w, const Arena& A, const FrJob& job,
                                   int32_t* dbg_gldm, int32_t* dbg_ngn,
                                   long long* dbg_ngs) {
   const int lane = lane_id();
