@@ -893,7 +893,10 @@ static __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& jo
       }
     }
     __syncwarp();
-    for (int a = lane; a < m; a += 32) marg[a] = 0;
+    for (int a = lane; a < m; a += 32) {  // leave the big region zero for the other families
+      marg[a] = 0;
+      prank[a] = 0;
+    }
     // difference and sum distributions (bins relative to the smallest level)
     unsigned dk = 0, sk = 0;
     unsigned long long dk2 = 0;
@@ -1146,7 +1149,155 @@ __device__ __forceinline__ void uf_unite(int* parent, int a, int b) {
   }
 }
 
-static __device__ void glszm_family(const Win& w, const Arena& A, int32_t* dbg_glszm) {
+// Per-lane partial sums over zones (level value i, size j): sum i, i^2,
+// j^2, and 1/j^2, 1/i^2, 1/(i^2 j^2), i^2/j^2, j^2/i^2, i^2 j^2.
+struct ZoneAcc {
+  unsigned si = 0, si2 = 0, sj2 = 0;
+  float fs[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sae lgl sal sah lal lah ze
+
+  __device__ __forceinline__ void add(unsigned i, unsigned j) {
+    si += i;
+    si2 += i * i;
+    sj2 += j * j;
+    const float fi2 = (float)(i * i), fj2 = (float)(j * j);
+    const float inv_i2 = __fdividef(1.f, fi2), inv_j2 = __fdividef(1.f, fj2);
+    fs[0] += inv_j2;
+    fs[1] += inv_i2;
+    fs[2] += inv_i2 * inv_j2;
+    fs[3] += fi2 * inv_j2;
+    fs[4] += fj2 * inv_i2;
+    fs[5] += fi2 * fj2;
+  }
+};
+
+// Bit masks over a cube of side S (bit p = (z S + y) S + x) for the
+// 26-neighbour dilation: kind 0: x != 0, 1: x != S-1, 2: y != 0, 3: y != S-1,
+// 4: inside the cube.
+template <int S>
+__host__ __device__ constexpr uint32_t cube_mask(int word, int kind) {
+  uint32_t m = 0;
+  for (int b = 0; b < 32; ++b) {
+    const int p = 32 * word + b;
+    if (p >= S * S * S) continue;
+    const int x = p % S, y = (p / S) % S;
+    const bool ok = kind == 0 ? x != 0 : kind == 1 ? x != S - 1 : kind == 2 ? y != 0
+                  : kind == 3 ? y != S - 1 : true;
+    if (ok) m |= 1u << b;
+  }
+  return m;
+}
+
+// Word i of the NW-word bit set f shifted towards higher (K > 0) or lower
+// (K < 0) bit indices by |K| bits.
+template <int NW, int K>
+__device__ __forceinline__ uint32_t shifted(const uint32_t (&f)[NW], int i) {
+  constexpr int A = K > 0 ? K : -K, Q = A / 32, R = A % 32;
+  if (K > 0) {
+    const uint32_t hi = i - Q >= 0 ? f[i - Q] : 0u;
+    const uint32_t lo = i - Q - 1 >= 0 ? f[i - Q - 1] : 0u;
+    return R ? __funnelshift_l(lo, hi, R) : hi;
+  } else {
+    const uint32_t lo = i + Q < NW ? f[i + Q] : 0u;
+    const uint32_t hi = i + Q + 1 < NW ? f[i + Q + 1] : 0u;
+    return R ? __funnelshift_r(lo, hi, R) : lo;
+  }
+}
+
+// o = (f dilated by the 26-neighbourhood, inside the cube) & lim, done as
+// three separable 3-tap dilations (x, then y, then z).
+template <int S, int NW>
+__device__ __forceinline__ void dilate26(const uint32_t (&f)[NW], const uint32_t (&lim)[NW],
+                                         uint32_t (&o)[NW]) {
+  uint32_t a[NW], b[NW];
+#pragma unroll
+  for (int i = 0; i < NW; ++i)
+    a[i] = f[i] | (shifted<NW, 1>(f, i) & cube_mask<S>(i, 0)) |
+           (shifted<NW, -1>(f, i) & cube_mask<S>(i, 1));
+#pragma unroll
+  for (int i = 0; i < NW; ++i)
+    b[i] = a[i] | (shifted<NW, S>(a, i) & cube_mask<S>(i, 2)) |
+           (shifted<NW, -S>(a, i) & cube_mask<S>(i, 3));
+#pragma unroll
+  for (int i = 0; i < NW; ++i)
+    o[i] = (b[i] | (shifted<NW, S * S>(b, i) & cube_mask<S>(i, 4)) | shifted<NW, -S * S>(b, i)) &
+           lim[i];
+}
+
+// Zones of V(v) for a window of side S: lane a owns compact level a (and
+// a + 32, ...): its level set as a bit mask (one ballot per 32 positions),
+// then repeatedly flood-fills from the lowest remaining voxel by 26-neighbour
+// dilations until the set stops growing; each fill is one zone.  Appends
+// zone keys (size << 8 | level) to A.kb and returns the zone count.
+template <int S>
+__device__ int glszm_zones_bits(const Win& w, const Arena& A, int* counter, ZoneAcc& z,
+                                unsigned& glnu, int32_t* dbg_glszm) {
+  constexpr int NW = (S * S * S + 31) / 32;
+  const int lane = lane_id();
+  if (lane == 0) *counter = 0;
+  __syncwarp();
+  for (int a0 = 0; a0 < w.m; a0 += 32) {
+    const int a = a0 + lane;
+    uint32_t L[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      const int p = 32 * k + lane;
+      const int lv = p < S * S * S ? (int)A.lvl[p] - 1 - a0 : -1;  // compact level - a0
+      uint32_t word = 0u;
+      const int top = min(32, w.m - a0);
+      for (int c = 0; c < top; ++c) {
+        const uint32_t bal = __ballot_sync(kFull, lv == c);
+        if (lane == c) word = bal;
+      }
+      L[k] = a < w.m ? word : 0u;
+    }
+    unsigned cnt = 0;
+    const unsigned i = a < w.m ? (unsigned)A.lev[a] : 0u;
+    while (true) {
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < NW; ++k) any |= L[k] != 0u;
+      if (!any) break;
+      uint32_t F[NW];
+      bool found = false;
+#pragma unroll
+      for (int k = 0; k < NW; ++k) {
+        F[k] = (!found && L[k]) ? (L[k] & (0u - L[k])) : 0u;
+        found |= L[k] != 0u;
+      }
+      while (true) {
+        uint32_t G[NW];
+        dilate26<S, NW>(F, L, G);
+        bool grew = false;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+          grew |= G[k] != F[k];
+          F[k] = G[k];
+        }
+        if (!grew) break;
+      }
+      unsigned size = 0;
+#pragma unroll
+      for (int k = 0; k < NW; ++k) {
+        size += __popc(F[k]);
+        L[k] &= ~F[k];
+      }
+      const int slot = atomicAdd(counter, 1);
+      A.kb[slot] = (size << 8) | (unsigned)a;
+      z.add(i, size);
+      ++cnt;
+      if (dbg_glszm) atomicAdd(&dbg_glszm[(size_t)(i - 1) * w.W + (size - 1)], 1);
+    }
+    glnu += cnt * cnt;
+  }
+  __syncwarp();
+  const int nz = *counter;
+  __syncwarp();
+  return nz;
+}
+
+// Zones by a lock-free union-find over the window (any window size).
+static __device__ int glszm_zones_uf(const Win& w, const Arena& A, ZoneAcc& z, unsigned& glnu,
+                              int32_t* dbg_glszm) {
   const int lane = lane_id();
   const int m = w.m;
   int* parent = (int*)(A.big + A.L.parent);
@@ -1161,11 +1312,11 @@ static __device__ void glszm_family(const Win& w, const Arena& A, int32_t* dbg_g
   for (int p = lane; p < w.W; p += 32) {
     const int a = A.lvl[p];
     if (!a) continue;
-    int z, y, x;
-    pos_to_zyx(w, p, z, y, x);
+    int zz, y, x;
+    pos_to_zyx(w, p, zz, y, x);
     for (int di = 0; di < kNumDirs; ++di) {
       const int dz = c_dirs[di][0], dy = c_dirs[di][1], dx = c_dirs[di][2];
-      if (!in_cube(w, z + dz, y + dy, x + dx)) continue;
+      if (!in_cube(w, zz + dz, y + dy, x + dx)) continue;
       const int q = p + dz * w.s2 + dy * w.s + dx;
       if (A.lvl[q] == a) uf_unite(parent, p, q);
     }
@@ -1178,8 +1329,6 @@ static __device__ void glszm_family(const Win& w, const Arena& A, int32_t* dbg_g
   __syncwarp();
   // zones: roots of V(v) components -> keys (size << 8 | compact level)
   int nz = 0;
-  unsigned si = 0, si2 = 0, sj2 = 0;
-  float fs[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sae lgl sal sah lal lah ze
   for (int base = 0; base < w.W; base += 32) {
     const int p = base + lane;
     bool root = false;
@@ -1193,26 +1342,46 @@ static __device__ void glszm_family(const Win& w, const Arena& A, int32_t* dbg_g
     if (root) {
       A.kb[nz + __popc(b & lanemask_lt())] = ((uint32_t)size << 8) | (uint32_t)(a - 1);
       const unsigned i = A.lev[a - 1];
-      const unsigned j = (unsigned)size;
-      si += i;
-      si2 += i * i;
-      sj2 += j * j;
-      const float fi2 = (float)(i * i), fj2 = (float)(j * j);
-      const float inv_i2 = __fdividef(1.f, fi2), inv_j2 = __fdividef(1.f, fj2);
-      fs[0] += inv_j2;
-      fs[1] += inv_i2;
-      fs[2] += inv_i2 * inv_j2;
-      fs[3] += fi2 * inv_j2;
-      fs[4] += fj2 * inv_i2;
-      fs[5] += fi2 * fj2;
+      z.add(i, (unsigned)size);
       atomicAdd(&zlv[a - 1], 1);
-      if (dbg_glszm) atomicAdd(&dbg_glszm[(size_t)(i - 1) * w.W + (j - 1)], 1);
+      if (dbg_glszm) atomicAdd(&dbg_glszm[(size_t)(i - 1) * w.W + (size - 1)], 1);
     }
     nz += __popc(b);
   }
   __syncwarp();
+  for (int a = lane; a < m; a += 32) {
+    const unsigned c = (unsigned)zlv[a];
+    zlv[a] = 0;
+    glnu += c * c;
+  }
+  // the big region is shared by the families, which count into it from zero
+  for (int p = lane; p < w.W; p += 32) {
+    parent[p] = 0;
+    zsz[p] = 0;
+  }
+  return nz;
+}
+
+static __device__ void glszm_family(const Win& w, const Arena& A, int32_t* dbg_glszm) {
+  const int lane = lane_id();
+  ZoneAcc z;
+  unsigned glnu = 0;
+  int* counter = (int*)(A.big + A.L.zlv);
+  int nz;
+  if (w.s == 3)
+    nz = glszm_zones_bits<3>(w, A, counter, z, glnu, dbg_glszm);
+  else if (w.s == 5)
+    nz = glszm_zones_bits<5>(w, A, counter, z, glnu, dbg_glszm);
+  else if (w.s == 7)
+    nz = glszm_zones_bits<7>(w, A, counter, z, glnu, dbg_glszm);
+  else
+    nz = glszm_zones_uf(w, A, z, glnu, dbg_glszm);
+  if (lane == 0) *counter = 0;
+  unsigned si = z.si, si2 = z.si2, sj2 = z.sj2;
+  float (&fs)[7] = z.fs;
+  __syncwarp();
   warp_sort(A.kb, nz);
-  unsigned sznu = 0, glnu = 0;
+  unsigned sznu = 0;
   for (int i = lane; i < nz; i += 32) {
     const uint32_t key = A.kb[i];
     if (i == 0 || A.kb[i - 1] != key) {
@@ -1224,22 +1393,12 @@ static __device__ void glszm_family(const Win& w, const Arena& A, int32_t* dbg_g
       sznu += c * c;
     }
   }
-  for (int a = lane; a < m; a += 32) {
-    const unsigned c = (unsigned)zlv[a];
-    zlv[a] = 0;
-    glnu += c * c;
-  }
   si = redux_u32(si);
   si2 = redux_u32(si2);
   sj2 = redux_u32(sj2);
   sznu = redux_u32(sznu);
   glnu = redux_u32(glnu);
   warp_sum_f32x<7>(fs);
-  // the big region is shared by the families, which count into it from zero
-  for (int p = lane; p < w.W; p += 32) {
-    parent[p] = 0;
-    zsz[p] = 0;
-  }
   const float N = (float)nz;
   const unsigned sj = (unsigned)w.nv;  // zone sizes add up to N_v
   float num = kNaNf, den = N;

@@ -51,6 +51,14 @@ def test_tiny_glcm_and_first_order_full():
     _check(img, mask, features=list(range(42)), disc_mode=0, bin_count=16, kernel_radius=1)
 
 
+def test_tiny_fbn24_r2_many_levels_per_window():
+    # uniform noise with 24 bins: most 5^3 windows hold 22-24 levels, the top
+    # of what the shared-memory arena takes (every family's matrices over
+    # high compact levels; MCC on more than 12 levels)
+    img, mask = synth.tiny(seed=1)
+    _check(img, mask, disc_mode=0, bin_count=24, kernel_radius=2)
+
+
 def test_tiny_all_93_full():
     img, mask = synth.tiny(seed=1)
     _check(img, mask, disc_mode=0, bin_count=16, kernel_radius=1)
