@@ -80,7 +80,7 @@ struct FrArena {
   int32_t off_st;     // uint16[264]     start of each level run in the sorted keys
   int32_t off_fv;     // float[96]       features of the current voxel
   int32_t off_acc;    // float[32] + int32[32]  per-direction accumulators
-  int32_t off_tmp;    // float[64]       per-direction scratch
+  int32_t off_tmp;    // float[64]       compensation terms of the direction sums
   int32_t off_big;    // family matrices (layout from (mc, bc, w))
   int32_t big_bytes;  // size of the shared big region
   int32_t p_max, w_max;
@@ -144,6 +144,7 @@ struct FrScalarArgs {
 struct BigLayout {
   int32_t cnt, marg, prank, sbin, dbin, vec;  // GLCM (vec: 4 float vectors of mc)
   int32_t mn, mres, slots;                    // GLCM MCC: n per direction, results, slots
+  int32_t csn, cst;                           // GLCM ClusterShade numerators (f64), totals
   int32_t rhist, rlv, rlen;                  // GLRLM
   int32_t parent, zsz, zlv;                  // GLSZM
   int32_t ghist, gj, ngn, ngs;               // GLDM / NGTDM
@@ -167,7 +168,9 @@ __host__ __device__ inline BigLayout fr_big_layout(int32_t mc, int32_t bc,
   L.mn = L.vec + 4 * mc * 4;
   L.mres = L.mn + 16 * 4;
   L.slots = L.mres + 16 * 4;
-  int32_t glcm_end = L.slots + kNumDirs * kSlot * 4;
+  L.csn = fr_align(L.slots + kNumDirs * kSlot * 4, 8);
+  L.cst = L.csn + 16 * 8;
+  int32_t glcm_end = L.cst + 16 * 4;
   // GLRLM
   L.rhist = 0;
   L.rlv = L.rhist + mc * 16 * 4;

@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(32 * kMaxConsumerWarps, 1)
   A.facc = (float*)(ab + args.arena.off_acc);
   A.nacc = (int*)(ab + args.arena.off_acc + 32 * 4);
   A.tmp = (float*)(ab + args.arena.off_tmp);
+  A.fcomp = A.tmp;
   char* smem_big = (char*)(ab + args.arena.off_big);
   char* slab_big = args.slab ? args.slab + ((size_t)blockIdx.x * NW + warp) * args.slab_stride
                              : nullptr;

@@ -31,6 +31,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "fr_device.cuh"
 #include "fr_internal.h"
@@ -89,6 +90,7 @@ struct Arena {
   uint16_t* st;  // run starts of the sorted keys
   float* fv;
   float* facc;
+  float* fcomp;  // rounding error of each facc sum (compensated summation)
   int* nacc;
   float* tmp;
   char* big;  // the selected big region
@@ -376,17 +378,23 @@ static __device__ void compact_levels(const Win& w, const Arena& A) {
   __syncwarp();
 }
 
-// Per-direction accumulation: lane f < nf adds finite v into facc[f].
+// Per-direction accumulation: lane f < nf adds finite v into facc[f].  The
+// sum is compensated (Knuth's TwoSum keeps each addition's rounding error in
+// fcomp): per-direction values of either sign can cancel to a mean far below
+// them (ClusterShade), where a plain fp32 sum loses the digits.
 __device__ __forceinline__ void acc_reset(const Arena& A) {
   const int lane = lane_id();
   A.facc[lane] = 0.f;
+  A.fcomp[lane] = 0.f;
   A.nacc[lane] = 0;
   __syncwarp();
 }
 __device__ __forceinline__ void acc_lane(const Arena& A, int nf, float v) {
   const int lane = lane_id();
   if (lane < nf && !isnan(v)) {
-    A.facc[lane] += v;
+    const float a = A.facc[lane], s = a + v, bv = s - a;
+    A.fcomp[lane] += (a - (s - bv)) + (v - bv);
+    A.facc[lane] = s;
     A.nacc[lane] += 1;
   }
 }
@@ -394,7 +402,8 @@ __device__ __forceinline__ void acc_store(const Arena& A, int nf, int f0) {
   __syncwarp();
   const int lane = lane_id();
   if (lane < nf)
-    A.fv[f0 + lane] = A.nacc[lane] ? __fdividef(A.facc[lane], (float)A.nacc[lane]) : kNaNf;
+    A.fv[f0 + lane] = A.nacc[lane] ? __fdividef(A.facc[lane] + A.fcomp[lane], (float)A.nacc[lane])
+                                   : kNaNf;
   __syncwarp();
 }
 
@@ -709,6 +718,13 @@ static __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& jo
     mres[lane] = kNaNf;
   }
   acc_reset(A);
+  // ClusterShade: per-direction values of either sign (hundreds, for
+  // near-symmetric windows) can average to ~1e-2, below what fp32 keeps
+  // after rounding each; their exact numerators (FP64) and totals are kept
+  // per direction and summed in FP64 after the loop
+  double* csn = (double*)(A.big + A.L.csn);
+  int* cst = (int*)(A.big + A.L.cst);
+  if (lane < kNumDirs) cst[lane] = 0;
   int np = 0;
   for (int di = 0; di < kNumDirs; ++di) {
     const int ddz = c_dirs[di][0] * job.delta, ddy = c_dirs[di][1] * job.delta,
@@ -947,7 +963,12 @@ static __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& jo
     if (lane == 0) { num = (float)a1; den = fT; }
     if (lane == 1) { num = (float)m1; den = fT; }
     if (lane == 2) { num = fs[11]; den = fT * fT * fT * fT * fT; }
-    if (lane == 3) { num = i128_to_f32(ce3); den = fT * fT * fT * fT; }
+    if (lane == 3) {
+      num = i128_to_f32(ce3);
+      den = fT * fT * fT * fT;
+      csn[ds] = i128_to_f64(ce3);
+      cst[ds] = T;
+    }
     if (lane == 4) { num = fs[10]; den = fT * fT * fT; }
     if (lane == 5) { num = (float)dk2; den = fT; }
     if (lane == 6) { num = (float)((long long)T * (long long)a1 - (long long)m1 * m1); den = (float)var_num; }
@@ -991,17 +1012,241 @@ static __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& jo
         }
       }
       A.facc[23] = s;
+      A.fcomp[23] = 0.f;
       A.nacc[23] = c;
     }
   }
   acc_store(A, want_mcc ? 24 : 23, 18);
+  {
+    __syncwarp();
+    const int t = lane < kNumDirs ? cst[lane] : 0;
+    double v = 0.0;
+    if (t > 0) {
+      const double dt = (double)t;
+      v = csn[lane] / (dt * dt * dt * dt);
+    }
+    const int n = __popc(__ballot_sync(kFull, t > 0));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (lane == 3 && n) A.fv[18 + 3] = (float)(v / (double)n);
+    if (lane < kNumDirs) cst[lane] = 0;  // leave the big region zero
+    __syncwarp();
+  }
 }
 
 // ------------------------------------------------------------------ GLRLM
+// ------------------------------------------------------------------ slice bit masks
+// For windows of side S <= 7 a set of window positions is S words, word z
+// holding slice z with bit y S + x (32-bit words up to S = 5, 64-bit at 7).
+// Lane a holds the set of compact level a; shifting a set along a direction
+// d moves whole words by dz and bits by dy S + dx.
+template <int S>
+struct SliceT {
+  using W = typename std::conditional<(S * S <= 32), uint32_t, unsigned long long>::type;
+  static constexpr int kChunks = (S * S + 31) / 32;
+  static __device__ __forceinline__ W full() { return (W)(((unsigned long long)1 << (S * S)) - 1ull); }
+  // in-slice positions whose row y + dy (column x + dx) stays inside
+  static __device__ __forceinline__ W rows_ok(int dy) {
+    constexpr unsigned long long row0 = ((unsigned long long)1 << S) - 1ull;
+    constexpr unsigned long long allr = ((unsigned long long)1 << (S * S)) - 1ull;
+    return (W)(dy > 0 ? (allr >> S) : dy < 0 ? (allr & ~row0) : allr);
+  }
+  static __device__ __forceinline__ W cols_ok(int dx) {
+    unsigned long long c = 0;
+#pragma unroll
+    for (int y = 0; y < S; ++y)
+      c |= (dx > 0 ? (((unsigned long long)1 << (S - 1)) - 1ull)
+                   : dx < 0 ? ((((unsigned long long)1 << S) - 1ull) & ~1ull)
+                            : (((unsigned long long)1 << S) - 1ull))
+           << (y * S);
+    return (W)c;
+  }
+};
+
+template <typename W>
+__device__ __forceinline__ W shift_bits(W x, int k) {  // bit b + k -> b (k may be < 0)
+  return k >= 0 ? (W)(x >> k) : (W)(x << (-k));
+}
+
+// One direction d = (dz, dy, dx), dz in {0, 1}, as shift parameters.
+template <int S>
+struct SliceDir {
+  using W = typename SliceT<S>::W;
+  int dz, k;
+  W mf, mb;  // u + d (u - d) inside, in-slice part
+  __device__ __forceinline__ SliceDir(int dz_, int dy, int dx) {
+    dz = dz_;
+    k = dy * S + dx;
+    mf = SliceT<S>::rows_ok(dy) & SliceT<S>::cols_ok(dx);
+    mb = SliceT<S>::rows_ok(-dy) & SliceT<S>::cols_ok(-dx);
+  }
+  // o(u) = x(u + d)
+  __device__ __forceinline__ void fwd(const W (&x)[S], W (&o)[S]) const {
+#pragma unroll
+    for (int z = 0; z < S; ++z) {
+      const W src = dz ? (z + 1 < S ? x[z + 1 < S ? z + 1 : z] : (W)0) : x[z];
+      o[z] = shift_bits<W>(src, k) & mf;
+    }
+  }
+  // o(u) = x(u - d)
+  __device__ __forceinline__ void bwd(const W (&x)[S], W (&o)[S]) const {
+#pragma unroll
+    for (int z = 0; z < S; ++z) {
+      const W src = dz ? (z >= 1 ? x[z >= 1 ? z - 1 : z] : (W)0) : x[z];
+      o[z] = shift_bits<W>(src, -k) & mb;
+    }
+  }
+};
+
+template <typename W>
+__device__ __forceinline__ int popc_w(W x) {
+  if (sizeof(W) == 8) return __popcll((unsigned long long)x);
+  return __popc((unsigned)x);
+}
+
+// This lane's compact-level set (level `lane`; empty past m) and the VOI set,
+// by one ballot per slice chunk and level.
+template <int S>
+__device__ __forceinline__ void slice_masks(const Win& w, const Arena& A,
+                                            typename SliceT<S>::W (&L)[S],
+                                            typename SliceT<S>::W (&V)[S]) {
+  using W = typename SliceT<S>::W;
+  const int lane = lane_id();
+#pragma unroll
+  for (int z = 0; z < S; ++z) {
+    W l = 0, v = 0;
+#pragma unroll
+    for (int c = 0; c < SliceT<S>::kChunks; ++c) {
+      const int bit = 32 * c + lane;
+      const int lv = bit < S * S ? (int)A.lvl[z * S * S + bit] : 0;
+      v |= (W)__ballot_sync(kFull, lv != 0) << (32 * c);
+      for (int a = 0; a < w.m; ++a) {
+        const unsigned bal = __ballot_sync(kFull, lv == a + 1);
+        if (lane == a) l |= (W)bal << (32 * c);
+      }
+    }
+    L[z] = l;
+    V[z] = v;
+  }
+}
+
+// GLRLM of windows of side S <= 5 with at most 32 levels: lane a counts the
+// runs of level a along each direction from its level set: starts are the
+// voxels whose predecessor u - d is not in the set, R_j the voxels that begin
+// a chain of j, so runs of length >= j number |starts & R_j|.
+template <int S>
+__device__ void glrlm_masks(const Win& w, const Arena& A, bool merged, int32_t* dbg_glrlm) {
+  using W = typename SliceT<S>::W;
+  const int lane = lane_id();
+  W L[S], V[S];
+  slice_masks<S>(w, A, L, V);
+  (void)V;
+  const bool ok = lane < w.m;
+  const unsigned i = ok ? (unsigned)A.lev[lane] : 1u;
+  const float fi2 = (float)(i * i), inv_i2 = __fdividef(1.f, fi2);
+  const float nvf = merged ? (float)(kNumDirs * w.nv) : (float)w.nv;
+  acc_reset(A);
+  unsigned h[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) h[j] = 0u;
+  for (int di = 0; di < kNumDirs; ++di) {
+    const SliceDir<S> D(c_dirs[di][0], c_dirs[di][1], c_dirs[di][2]);
+    W st[S], R[S], T[S];
+    D.bwd(L, T);
+    unsigned c[S + 1];
+    c[0] = 0u;
+#pragma unroll
+    for (int z = 0; z < S; ++z) {
+      st[z] = L[z] & ~T[z];
+      R[z] = L[z];
+      c[0] += (unsigned)popc_w<W>(st[z]);
+    }
+#pragma unroll
+    for (int j = 1; j < S; ++j) {
+      D.fwd(R, T);
+      c[j] = 0u;
+#pragma unroll
+      for (int z = 0; z < S; ++z) {
+        R[z] = L[z] & T[z];
+        c[j] += (unsigned)popc_w<W>(st[z] & R[z]);
+      }
+    }
+    c[S] = 0u;
+#pragma unroll
+    for (int j = 0; j < S; ++j) h[j] += c[j] - c[j + 1];  // runs of length j + 1
+    if (merged && di < kNumDirs - 1) continue;
+    const int ds = merged ? 0 : di;
+    unsigned row = 0, si = 0, si2 = 0, sj = 0, sj2 = 0;
+    float fs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sre lgl srl srh lrl lrh
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const unsigned cnt = h[j];
+      const unsigned J = (unsigned)(j + 1);
+      const float fc = (float)cnt, fj2 = (float)(J * J), inv_j2 = 1.f / (float)(J * J);
+      row += cnt;
+      sj += cnt * J;
+      sj2 += cnt * J * J;
+      fs[0] += fc * inv_j2;
+      fs[1] += fc * inv_i2;
+      fs[2] += fc * inv_i2 * inv_j2;
+      fs[3] += fc * fi2 * inv_j2;
+      fs[4] += fc * fj2 * inv_i2;
+      fs[5] += fc * fi2 * fj2;
+      if (dbg_glrlm && cnt) dbg_glrlm[((size_t)ds * w.ng + (i - 1)) * w.s + j] = (int)cnt;
+    }
+    si = row * i;
+    si2 = row * i * i;
+    const unsigned nr = redux_u32(row);
+    unsigned rlnu = 0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const unsigned col = redux_u32(h[j]);
+      rlnu += col * col;
+    }
+    float ent = 0.f;
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+      if (h[j]) ent += ent_term((int)h[j], (int)nr);
+    const unsigned glnu = redux_u32(row * row);
+    si = redux_u32(si);
+    si2 = redux_u32(si2);
+    sj = redux_u32(sj);
+    sj2 = redux_u32(sj2);
+    float fsr[7] = {fs[0], fs[1], fs[2], fs[3], fs[4], fs[5], ent};
+    warp_sum_f32x<7>(fsr);
+    const float N = (float)nr;
+    float num = kNaNf, den = N;
+    if (lane == 0) { num = fsr[0]; }
+    if (lane == 1) { num = (float)sj2; }
+    if (lane == 2) { num = (float)glnu; }
+    if (lane == 3) { num = (float)glnu; den = N * N; }
+    if (lane == 4) { num = (float)rlnu; }
+    if (lane == 5) { num = (float)rlnu; den = N * N; }
+    if (lane == 6) { num = N; den = nvf; }
+    if (lane == 7) { num = (float)((long long)nr * si2 - (long long)si * si); den = N * N; }
+    if (lane == 8) { num = (float)((long long)nr * sj2 - (long long)sj * sj); den = N * N; }
+    if (lane == 9) { num = fsr[6]; den = 1.f; }
+    if (lane == 10) { num = fsr[1]; }
+    if (lane == 11) { num = (float)si2; }
+    if (lane == 12) { num = fsr[2]; }
+    if (lane == 13) { num = fsr[3]; }
+    if (lane == 14) { num = fsr[4]; }
+    if (lane == 15) { num = fsr[5]; }
+    acc_lane(A, 16, lane_quot(num, den));
+#pragma unroll
+    for (int j = 0; j < S; ++j) h[j] = 0u;
+  }
+  acc_store(A, 16, 42);
+}
+
 // merged: the 13 directions' runs go into one matrix, whose features are
 // taken once (RunPercentage over 13 N_v: each voxel lies on one run per
 // direction).
 static __device__ void glrlm_family(const Win& w, const Arena& A, bool merged, int32_t* dbg_glrlm) {
+  if (w.m <= 32) {
+    if (w.s == 3) return glrlm_masks<3>(w, A, merged, dbg_glrlm);
+    if (w.s == 5) return glrlm_masks<5>(w, A, merged, dbg_glrlm);
+  }
   const int lane = lane_id();
   const int m = w.m;
   int* hist = (int*)(A.big + A.L.rhist);  // [mc][16]
