@@ -675,366 +675,6 @@ __device__ __forceinline__ float rho_reg(const float* __restrict__ P) {
   return 0.5f * (lo + hi);
 }
 
-// (1 + d) ln(1 + d) - d >= 0 (d >= -1) without the cancellation near d = 0:
-// there its Taylor series sum_{k>=2} (-d)^k / (k (k - 1)), cut after d^9.
-__device__ __forceinline__ float kl_term(float d) {
-  if (fabsf(d) < 0.125f)
-    return d * d *
-           (0.5f + d * (-1.f / 6.f +
-                        d * (1.f / 12.f +
-                             d * (-1.f / 20.f +
-                                  d * (1.f / 30.f +
-                                       d * (-1.f / 42.f + d * (1.f / 56.f + d * (-1.f / 72.f))))))));
-  return (1.f + d) * log1pf(d) - d;
-}
-
-// ------------------------------------------------------------------ GLCM
-static __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
-                            int32_t* dbg_glcm) {
-  const int lane = lane_id();
-  const int m = w.m, mc = A.mc;
-  int* cnt = (int*)(A.big + A.L.cnt);
-  int* marg = (int*)(A.big + A.L.marg);
-  int* prank = (int*)(A.big + A.L.prank);  // rank of a present level
-  int* sbin = (int*)(A.big + A.L.sbin);
-  int* dbin = (int*)(A.big + A.L.dbin);
-  float* vv = (float*)(A.big + A.L.vec);
-  float* ww = vv + mc;
-  float* dd = ww + mc;
-  float* ee = dd + mc;
-  int* mn = (int*)(A.big + A.L.mn);
-  float* mres = (float*)(A.big + A.L.mres);
-  float* slots = (float*)(A.big + A.L.slots);
-  const bool want_mcc = (job.families & kFamMCC) != 0;
-  const float ngf = (float)w.ng;
-  Magic mm;
-  mm.init((unsigned)m);
-  const int mm2 = m * m;
-  // merged aggregation: the 13 directions' pairs go into one matrix, whose
-  // features (and MCC, in slot 0) are taken once
-  const bool merged = job.agg == 1;
-  if (merged && want_mcc && lane < kNumDirs) {
-    mn[lane] = 0;
-    mres[lane] = kNaNf;
-  }
-  acc_reset(A);
-  // ClusterShade: per-direction values of either sign (hundreds, for
-  // near-symmetric windows) can average to ~1e-2, below what fp32 keeps
-  // after rounding each; their exact numerators (FP64) and totals are kept
-  // per direction and summed in FP64 after the loop
-  double* csn = (double*)(A.big + A.L.csn);
-  int* cst = (int*)(A.big + A.L.cst);
-  if (lane < kNumDirs) cst[lane] = 0;
-  int np = 0;
-  for (int di = 0; di < kNumDirs; ++di) {
-    const int ddz = c_dirs[di][0] * job.delta, ddy = c_dirs[di][1] * job.delta,
-              ddx = c_dirs[di][2] * job.delta;
-    const int off = ddz * w.s2 + ddy * w.s + ddx;
-    // pairs -> upper-triangle counts over compact indices (equal keys merged)
-    if (!merged) np = 0;
-    for (int base = 0; base < w.W; base += 32) {
-      const int p = base + lane;
-      int key = -1;
-      if (p < w.W) {
-        const int a = A.lvl[p];
-        if (a) {
-          int z, y, x;
-          pos_to_zyx(w, p, z, y, x);
-          if (in_cube(w, z + ddz, y + ddy, x + ddx)) {
-            const int b = A.lvl[p + off];
-            if (b) key = (min(a, b) - 1) * mc + (max(a, b) - 1);
-          }
-        }
-      }
-      const unsigned act = __ballot_sync(kFull, key >= 0);
-      if (key >= 0) {
-        const unsigned grp = __match_any_sync(act, key);
-        if ((grp & lanemask_lt()) == 0) atomicAdd(&cnt[key], __popc(grp));
-      }
-      np += __popc(act);
-    }
-    __syncwarp();
-    if (merged && di < kNumDirs - 1) continue;
-    const int ds = merged ? 0 : di;  // slot / record of this matrix
-    if (np == 0) {
-      if (lane == 0) {
-        mn[ds] = 0;
-        mres[ds] = kNaNf;
-      }
-      acc_lane(A, 23, kNaNf);
-      continue;
-    }
-    const int T = 2 * np;
-    const float fT = (float)T;
-    // marginals (lane a sums row a of the symmetric matrix) and present list
-    // 64-bit where a merged matrix (13 directions, up to 13 x 3375 pairs)
-    // can pass 2^32
-    unsigned m1 = 0;
-    unsigned long long m2 = 0;
-    float hx = 0.f;
-    int present = 0;
-    for (int a0 = 0; a0 < m; a0 += 32) {
-      const int a = a0 + lane;
-      int c = 0;
-      if (a < m) {
-        for (int b = 0; b < m; ++b)
-          c += b > a ? cnt[a * mc + b] : (b == a ? 2 * cnt[a * mc + a] : cnt[b * mc + a]);
-        marg[a] = c;
-        if (c) {
-          const unsigned i = A.lev[a];
-          m1 += i * (unsigned)c;
-          m2 += (unsigned long long)(i * i) * (unsigned)c;
-          hx += ent_term(c, T);
-        }
-      }
-      const unsigned pb = __ballot_sync(kFull, c > 0);
-      if (c > 0) prank[a] = present + __popc(pb & lanemask_lt());
-      present += __popc(pb);
-    }
-    m1 = redux_u32(m1);
-    m2 = merged ? warp_sum_u64(m2) : redux_u32((unsigned)m2);  // < 2^32 per direction
-    // MCC matrix of up to kCapL present levels: written by the entries pass
-    // into this direction's slot (zero first: the padding beyond them)
-    const bool slot = want_mcc && present >= 2 && present <= kCapL;
-    // counts are cleared as the entries pass reads them, unless the
-    // many-level MCC solve still needs them
-    const bool clear_now = !want_mcc || present <= kCapL;
-    float* P = slots + ds * kSlot;
-    const float invT = __fdividef(1.f, fT);
-    if (slot)
-      for (int t = lane; t < kSlot; t += 32) P[t] = 0.f;
-    __syncwarp();
-    // entries: linear sums, entropies, mutual information, sum / difference
-    // bins, the MCC slot
-    unsigned long long a1 = 0, e2 = 0, mi0 = 0;
-    unsigned maxc = 0;
-    // MI = sum over all level pairs of p ln(p/q) - p + q (q = p_a p_b; the
-    // extra terms sum to zero), every term >= 0: q g(p/q) where p > 0, and
-    // q where p = 0 (its sum kept exact in mi0 T^2); nats until the end
-    float hxy = 0.f, mi = 0.f;
-    const float fT2 = fT * fT;
-    for (int t0 = 0; t0 < mm2; t0 += 32) {
-      const int t = t0 + lane;
-      if (t >= mm2) continue;
-      const int a = (int)mm.div((unsigned)t), b = t - a * m;
-      if (b < a) continue;
-      const int n = cnt[a * mc + b];
-      if (!n) {
-        const int ca = marg[a], cb = marg[b];
-        if (ca && cb) {
-          // an empty pair of present levels: its q = p_a p_b enters MI, and
-          // S - u u^T is dense there (-u_a u_b)
-          const long long cc = (long long)ca * cb;
-          mi0 += (a == b ? 1ull : 2ull) * (unsigned long long)cc;
-          if (slot)
-            P[pk(kCapL, prank[a], prank[b])] =
-                (float)(-cc) * rsqrtf((float)ca * (float)cb) * invT;
-        }
-        continue;
-      }
-      const unsigned i = A.lev[a], j = A.lev[b];
-      const int C = (a == b) ? 2 * n : n;
-      const unsigned mult = (a == b) ? 1u : 2u;
-      a1 += (unsigned long long)(mult * (unsigned)C) * (i * j);
-      e2 += (unsigned long long)(mult * (unsigned)C) * (unsigned)C;
-      maxc = max(maxc, (unsigned)C);
-      const float fm = (float)mult;
-      hxy += fm * ent_term(C, T);
-      const int ca = marg[a], cb = marg[b];
-      const long long ct = (long long)C * T, cc = (long long)ca * cb;
-      if (ct != cc)  // p = p_x p_y exactly contributes nothing
-        mi += fm * __fdividef((float)cc, fT2) * kl_term(__fdividef((float)(ct - cc), (float)cc));
-      if (clear_now) cnt[a * mc + b] = 0;
-      // A(a', b') = (C T - c_a c_b) / (T sqrt(c_a c_b)) over present ranks
-      if (slot)
-        P[pk(kCapL, prank[a], prank[b])] =
-            (float)(ct - cc) * rsqrtf((float)ca * (float)cb) * invT;
-      atomicAdd(&sbin[i + j - 2 * w.lev0], 2 * n);
-      atomicAdd(&dbin[j - i], 2 * n);
-      if (dbg_glcm) {
-        int32_t* g = dbg_glcm + (size_t)ds * w.ng * w.ng;
-        g[(i - 1) * w.ng + (j - 1)] = C;
-        g[(j - 1) * w.ng + (i - 1)] = C;
-      }
-    }
-    if (merged) {
-      a1 = warp_sum_u64(a1);
-      e2 = warp_sum_u64(e2);
-      mi0 = warp_sum_u64(mi0);
-    } else {  // one direction: each < 2^32
-      a1 = redux_u32((unsigned)a1);
-      e2 = redux_u32((unsigned)e2);
-      mi0 = redux_u32((unsigned)mi0);
-    }
-    maxc = __reduce_max_sync(kFull, maxc);
-    __syncwarp();
-    // MCC: the deflated A = S - u u^T, S = D^-1/2 P D^-1/2 over present levels
-    if (want_mcc) {
-      const int nd = present;
-      if (nd < 2) {
-        if (lane == 0) {
-          mn[ds] = 0;
-          mres[ds] = kNaNf;
-        }
-      } else if (slot) {
-        if (lane == 0) mn[ds] = nd;  // solved after the 13 directions
-      } else {
-        // many levels: warp-cooperative solve now, on S in place of the counts
-        float* S = (float*)cnt;
-        for (int t = lane; t < mm2; t += 32) {
-          const int a = (int)mm.div((unsigned)t), b = t - a * m;
-          if (b < a) continue;
-          const int n = cnt[a * mc + b];
-          const int ca = marg[a], cb = marg[b];
-          float v = 0.f;
-          if (ca && cb) {
-            const int C = (a == b) ? 2 * n : n;
-            const long long num = (long long)C * T - (long long)ca * cb;
-            v = __fdividef((float)num * rsqrtf((float)ca * (float)cb), fT);
-          }
-          S[a * mc + b] = v;
-          S[b * mc + a] = v;
-        }
-        __syncwarp();
-        const float rho = spectral_radius(S, m, mc, vv, ww, dd, ee);
-        if (lane == 0) {
-          mn[ds] = 0;
-          mres[ds] = rho;
-        }
-        __syncwarp();
-        for (int t = lane; t < mm2; t += 32) {
-          const int a = (int)mm.div((unsigned)t);
-          cnt[a * mc + (t - a * m)] = 0;
-        }
-      }
-    }
-    __syncwarp();
-    for (int a = lane; a < m; a += 32) {  // leave the big region zero for the other families
-      marg[a] = 0;
-      prank[a] = 0;
-    }
-    // difference and sum distributions (bins relative to the smallest level)
-    unsigned dk = 0, sk = 0;
-    unsigned long long dk2 = 0;
-    float de = 0.f, idm = 0.f, idmn = 0.f, idd = 0.f, idn = 0.f, iv = 0.f, se = 0.f,
-          ce2 = 0.f, ce4 = 0.f;
-    __int128 ce3 = 0;
-    const int nb = 2 * w.R + 1;
-    for (int k = lane; k < nb; k += 32) {
-      if (k <= w.R) {
-        const int c = dbin[k];
-        if (c) {
-          dbin[k] = 0;
-          const float fk = (float)k, fc = (float)c;
-          dk += (unsigned)(k * c);
-          dk2 += (unsigned long long)(k * k) * (unsigned)c;
-          de += ent_term(c, T);
-          idm += __fdividef(fc, 1.f + fk * fk);
-          idmn += __fdividef(fc, 1.f + __fdividef(fk * fk, ngf * ngf));
-          idd += __fdividef(fc, 1.f + fk);
-          idn += __fdividef(fc, 1.f + __fdividef(fk, ngf));
-          if (k) iv += __fdividef(fc, fk * fk);
-        }
-      }
-      const int c = sbin[k];
-      if (c) {
-        sbin[k] = 0;
-        const int kk = k + 2 * w.lev0;
-        sk += (unsigned)(kk * c);
-        se += ent_term(c, T);
-        // T (k - 2 mu): |e| < 2^24 per direction, < 2^26 merged
-        const int e = T * kk - 2 * (int)m1;
-        const float fe = (float)e, fe2 = fe * fe;
-        ce2 += (float)c * fe2;
-        ce4 += (float)c * fe2 * fe2;
-        ce3 += (__int128)((long long)e * e) * ((long long)c * e);
-      }
-    }
-    dk = redux_u32(dk);
-    dk2 = merged ? warp_sum_u64(dk2) : redux_u32((unsigned)dk2);
-    sk = redux_u32(sk);
-    ce3 = warp_sum_i128(ce3);
-    float fs[12] = {hx, hxy, mi, de, idm, idmn, idd, idn, iv, se, ce2, ce4};
-    warp_sum_f32x<12>(fs);
-    fs[2] = (fs[2] + __fdividef((float)mi0, fT2)) * 1.44269504088896341f;  // bits
-    // one lane per feature
-    float num = kNaNf, den = 1.f;
-    const long long var_num = (long long)T * (long long)m2 - (long long)m1 * m1;  // T^2 sigma^2
-    if (lane == 0) { num = (float)a1; den = fT; }
-    if (lane == 1) { num = (float)m1; den = fT; }
-    if (lane == 2) { num = fs[11]; den = fT * fT * fT * fT * fT; }
-    if (lane == 3) {
-      num = i128_to_f32(ce3);
-      den = fT * fT * fT * fT;
-      csn[ds] = i128_to_f64(ce3);
-      cst[ds] = T;
-    }
-    if (lane == 4) { num = fs[10]; den = fT * fT * fT; }
-    if (lane == 5) { num = (float)dk2; den = fT; }
-    if (lane == 6) { num = (float)((long long)T * (long long)a1 - (long long)m1 * m1); den = (float)var_num; }
-    if (lane == 7) { num = (float)dk; den = fT; }
-    if (lane == 8) { num = fs[3]; }
-    if (lane == 9) { num = (float)((long long)T * (long long)dk2 - (long long)dk * dk); den = fT * fT; }
-    if (lane == 10) { num = (float)e2; den = fT * fT; }
-    if (lane == 11) { num = fs[1]; }
-    if (lane == 12) { num = -fs[2]; den = fs[0]; }
-    if (lane == 13) { num = sqrtf(fmaxf(0.f, -expm1f(-2.f * fs[2]))); }
-    if (lane == 14) { num = fs[4]; den = fT; }
-    if (lane == 15) { num = fs[5]; den = fT; }
-    if (lane == 16) { num = fs[6]; den = fT; }
-    if (lane == 17) { num = fs[7]; den = fT; }
-    if (lane == 18) { num = fs[8]; den = fT; }
-    if (lane == 19) { num = (float)maxc; den = fT; }
-    if (lane == 20) { num = (float)sk; den = fT; }
-    if (lane == 21) { num = fs[9]; }
-    if (lane == 22) { num = (float)var_num; den = fT * fT; }
-    acc_lane(A, 23, lane_quot(num, den));
-  }
-  __syncwarp();
-  if (want_mcc) {
-    // one register-resident size for the warp: the smallest that holds every
-    // direction's matrix (zero padding leaves the radius unchanged)
-    const int nl = (lane < kNumDirs) ? mn[lane] : 0;
-    const int nmax = __reduce_max_sync(kFull, nl);
-    if (nl >= 2) {
-      const float* P = slots + lane * kSlot;
-      mres[lane] = nmax <= 4 ? rho_reg<4>(P) : nmax <= 8 ? rho_reg<8>(P) : rho_reg<kCapL>(P);
-    }
-    __syncwarp();
-    if (lane == 23) {
-      float s = 0.f;
-      int c = 0;
-      for (int d = 0; d < kNumDirs; ++d) {
-        const float v = mres[d];
-        if (!isnan(v)) {
-          s += v;
-          ++c;
-        }
-      }
-      A.facc[23] = s;
-      A.fcomp[23] = 0.f;
-      A.nacc[23] = c;
-    }
-  }
-  acc_store(A, want_mcc ? 24 : 23, 18);
-  {
-    __syncwarp();
-    const int t = lane < kNumDirs ? cst[lane] : 0;
-    double v = 0.0;
-    if (t > 0) {
-      const double dt = (double)t;
-      v = csn[lane] / (dt * dt * dt * dt);
-    }
-    const int n = __popc(__ballot_sync(kFull, t > 0));
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if (lane == 3 && n) A.fv[18 + 3] = (float)(v / (double)n);
-    if (lane < kNumDirs) cst[lane] = 0;  // leave the big region zero
-    __syncwarp();
-  }
-}
-
-// ------------------------------------------------------------------ GLRLM
 // ------------------------------------------------------------------ slice bit masks
 // For windows of side S <= 7 a set of window positions is S words, word z
 // holding slice z with bit y S + x (32-bit words up to S = 5, 64-bit at 7).
@@ -1130,6 +770,489 @@ __device__ __forceinline__ void slice_masks(const Win& w, const Arena& A,
   }
 }
 
+// (1 + d) ln(1 + d) - d >= 0 (d >= -1) without the cancellation near d = 0:
+// there its Taylor series sum_{k>=2} (-d)^k / (k (k - 1)), cut after d^9.
+__device__ __forceinline__ float kl_term(float d) {
+  if (fabsf(d) < 0.125f)
+    return d * d *
+           (0.5f + d * (-1.f / 6.f +
+                        d * (1.f / 12.f +
+                             d * (-1.f / 20.f +
+                                  d * (1.f / 30.f +
+                                       d * (-1.f / 42.f + d * (1.f / 56.f + d * (-1.f / 72.f))))))));
+  return (1.f + d) * log1pf(d) - d;
+}
+
+// ------------------------------------------------------------------ GLCM
+// After the 13 directions: the deferred MCC solves (one lane per direction),
+// the direction means, and ClusterShade's FP64 mean.
+static __device__ void glcm_finish(const Arena& A, bool want_mcc, int* mn, float* mres,
+                                   float* slots, double* csn, int* cst) {
+  const int lane = lane_id();
+  __syncwarp();
+  if (want_mcc) {
+    // one register-resident size for the warp: the smallest that holds every
+    // direction's matrix (zero padding leaves the radius unchanged)
+    const int nl = (lane < kNumDirs) ? mn[lane] : 0;
+    const int nmax = __reduce_max_sync(kFull, nl);
+    if (nl >= 2) {
+      const float* P = slots + lane * kSlot;
+      mres[lane] = nmax <= 4 ? rho_reg<4>(P) : nmax <= 8 ? rho_reg<8>(P) : rho_reg<kCapL>(P);
+    }
+    __syncwarp();
+    if (lane == 23) {
+      float s = 0.f;
+      int c = 0;
+      for (int d = 0; d < kNumDirs; ++d) {
+        const float v = mres[d];
+        if (!isnan(v)) {
+          s += v;
+          ++c;
+        }
+      }
+      A.facc[23] = s;
+      A.fcomp[23] = 0.f;
+      A.nacc[23] = c;
+    }
+  }
+  acc_store(A, want_mcc ? 24 : 23, 18);
+  {
+    __syncwarp();
+    const int t = lane < kNumDirs ? cst[lane] : 0;
+    double v = 0.0;
+    if (t > 0) {
+      const double dt = (double)t;
+      v = csn[lane] / (dt * dt * dt * dt);
+    }
+    const int n = __popc(__ballot_sync(kFull, t > 0));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (lane == 3 && n) A.fv[18 + 3] = (float)(v / (double)n);
+    if (lane < kNumDirs) cst[lane] = 0;  // leave the big region zero
+    __syncwarp();
+  }
+}
+
+// S > 0: windows of side S with at most 32 levels, distance 1, per-direction
+// aggregation: pair counts from level bit masks (lane a holds level a's set;
+// a pair lane counts |L_a & fwd(L_b)| + |L_b & fwd(L_a)|), so there is no
+// shared-memory count matrix.  S == 0: any window; pairs counted into a
+// shared-memory matrix of compact levels.
+template <int S>
+static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJob& job,
+                                        int32_t* dbg_glcm) {
+  const int lane = lane_id();
+  const int m = w.m, mc = A.mc;
+  int* cnt = (int*)(A.big + A.L.cnt);
+  int* marg = (int*)(A.big + A.L.marg);
+  int* prank = (int*)(A.big + A.L.prank);  // rank of a present level
+  int* sbin = (int*)(A.big + A.L.sbin);
+  int* dbin = (int*)(A.big + A.L.dbin);
+  float* vv = (float*)(A.big + A.L.vec);
+  float* ww = vv + mc;
+  float* dd = ww + mc;
+  float* ee = dd + mc;
+  int* mn = (int*)(A.big + A.L.mn);
+  float* mres = (float*)(A.big + A.L.mres);
+  float* slots = (float*)(A.big + A.L.slots);
+  const bool want_mcc = (job.families & kFamMCC) != 0;
+  const float ngf = (float)w.ng;
+  Magic mm;
+  mm.init((unsigned)m);
+  const int mm2 = m * m;
+  // merged aggregation: the 13 directions' pairs go into one matrix, whose
+  // features (and MCC, in slot 0) are taken once
+  const bool merged = job.agg == 1;
+  if (merged && want_mcc && lane < kNumDirs) {
+    mn[lane] = 0;
+    mres[lane] = kNaNf;
+  }
+  acc_reset(A);
+  // ClusterShade: per-direction values of either sign (hundreds, for
+  // near-symmetric windows) can average to ~1e-2, below what fp32 keeps
+  // after rounding each; their exact numerators (FP64) and totals are kept
+  // per direction and summed in FP64 after the loop
+  double* csn = (double*)(A.big + A.L.csn);
+  int* cst = (int*)(A.big + A.L.cst);
+  if (lane < kNumDirs) cst[lane] = 0;
+  constexpr int SS = S > 0 ? S : 1;
+  using W = typename SliceT<SS>::W;
+  W Lm[SS], Vm[SS];
+  if constexpr (S > 0) slice_masks<S>(w, A, Lm, Vm);
+  const int npairs = m * (m + 1) / 2;
+  int np = 0;
+  for (int di = 0; di < kNumDirs; ++di) {
+    const int ddz = c_dirs[di][0] * job.delta, ddy = c_dirs[di][1] * job.delta,
+              ddx = c_dirs[di][2] * job.delta;
+    const int off = ddz * w.s2 + ddy * w.s + ddx;
+    // pairs -> upper-triangle counts over compact indices (equal keys merged)
+    if (!merged) np = 0;
+    W fL[SS];        // mask path: this lane's level set moved back along d
+    unsigned cmask = 0;  // mask path: this lane's marginal count
+    if constexpr (S > 0) {
+      const SliceDir<S> D(c_dirs[di][0], c_dirs[di][1], c_dirs[di][2]);
+      W fV[S], bV[S];
+      D.fwd(Lm, fL);
+      D.fwd(Vm, fV);
+      D.bwd(Vm, bV);
+      unsigned npz = 0;
+#pragma unroll
+      for (int z = 0; z < S; ++z) {
+        cmask += (unsigned)(popc_w<W>(Lm[z] & fV[z]) + popc_w<W>(Lm[z] & bV[z]));
+        npz += (unsigned)popc_w<W>(Vm[z] & fV[z]);
+      }
+      np = (int)npz;
+    }
+    for (int base = 0; S == 0 && base < w.W; base += 32) {
+      const int p = base + lane;
+      int key = -1;
+      if (p < w.W) {
+        const int a = A.lvl[p];
+        if (a) {
+          int z, y, x;
+          pos_to_zyx(w, p, z, y, x);
+          if (in_cube(w, z + ddz, y + ddy, x + ddx)) {
+            const int b = A.lvl[p + off];
+            if (b) key = (min(a, b) - 1) * mc + (max(a, b) - 1);
+          }
+        }
+      }
+      const unsigned act = __ballot_sync(kFull, key >= 0);
+      if (key >= 0) {
+        const unsigned grp = __match_any_sync(act, key);
+        if ((grp & lanemask_lt()) == 0) atomicAdd(&cnt[key], __popc(grp));
+      }
+      np += __popc(act);
+    }
+    __syncwarp();
+    if (merged && di < kNumDirs - 1) continue;
+    const int ds = merged ? 0 : di;  // slot / record of this matrix
+    if (np == 0) {
+      if (lane == 0) {
+        mn[ds] = 0;
+        mres[ds] = kNaNf;
+      }
+      acc_lane(A, 23, kNaNf);
+      continue;
+    }
+    const int T = 2 * np;
+    const float fT = (float)T;
+    // marginals (lane a sums row a of the symmetric matrix) and present list
+    // 64-bit where a merged matrix (13 directions, up to 13 x 3375 pairs)
+    // can pass 2^32
+    unsigned m1 = 0;
+    unsigned long long m2 = 0;
+    float hx = 0.f;
+    int present = 0;
+    int prank_l = 0;  // mask path: rank of this lane's level among present ones
+    for (int a0 = 0; a0 < m; a0 += 32) {
+      const int a = a0 + lane;
+      int c = 0;
+      if (a < m) {
+        if constexpr (S > 0) {
+          c = (int)cmask;
+        } else {
+          for (int b = 0; b < m; ++b)
+            c += b > a ? cnt[a * mc + b] : (b == a ? 2 * cnt[a * mc + a] : cnt[b * mc + a]);
+          marg[a] = c;
+        }
+        if (c) {
+          const unsigned i = A.lev[a];
+          m1 += i * (unsigned)c;
+          m2 += (unsigned long long)(i * i) * (unsigned)c;
+          hx += ent_term(c, T);
+        }
+      }
+      const unsigned pb = __ballot_sync(kFull, c > 0);
+      if constexpr (S > 0) {
+        prank_l = __popc(pb & lanemask_lt());
+      } else {
+        if (c > 0) prank[a] = present + __popc(pb & lanemask_lt());
+      }
+      present += __popc(pb);
+    }
+    m1 = redux_u32(m1);
+    m2 = merged ? warp_sum_u64(m2) : redux_u32((unsigned)m2);  // < 2^32 per direction
+    // MCC matrix of up to kCapL present levels: written by the entries pass
+    // into this direction's slot (zero first: the padding beyond them)
+    const bool slot = want_mcc && present >= 2 && present <= kCapL;
+    // counts are cleared as the entries pass reads them, unless the
+    // many-level MCC solve still needs them
+    const bool clear_now = !want_mcc || present <= kCapL;
+    // mask path, many levels: the pair lanes write S - u u^T for the
+    // warp-cooperative solve into the (zero) count region
+    const bool fill_s = S > 0 && want_mcc && present > kCapL;
+    float* Sm = (float*)cnt;
+    float* P = slots + ds * kSlot;
+    const float invT = __fdividef(1.f, fT);
+    if (slot)
+      for (int t = lane; t < kSlot; t += 32) P[t] = 0.f;
+    __syncwarp();
+    // entries: linear sums, entropies, mutual information, sum / difference
+    // bins, the MCC slot
+    unsigned long long a1 = 0, e2 = 0, mi0 = 0;
+    unsigned maxc = 0;
+    // MI = sum over all level pairs of p ln(p/q) - p + q (q = p_a p_b; the
+    // extra terms sum to zero), every term >= 0: q g(p/q) where p > 0, and
+    // q where p = 0 (its sum kept exact in mi0 T^2); nats until the end
+    float hxy = 0.f, mi = 0.f;
+    const float fT2 = fT * fT;
+    if constexpr (S > 0) {
+      // one lane per level pair (a <= b), 32 pairs a round
+      for (int t0 = 0; t0 < npairs; t0 += 32) {
+        const int t = t0 + lane;
+        const bool valid = t < npairs;
+        int a = 0, b = 0;
+        if (valid) {
+          // row a of the packed upper triangle: start(a) = a m - a (a - 1) / 2
+          const float q = (float)(2 * m + 1);
+          a = (int)((q - sqrtf(q * q - 8.f * (float)t)) * 0.5f);
+          a = max(0, min(a, m - 1));
+          while (a + 1 < m && (a + 1) * m - (((a + 1) * a) >> 1) <= t) ++a;
+          while (a > 0 && a * m - ((a * (a - 1)) >> 1) > t) --a;
+          b = a + (t - (a * m - ((a * (a - 1)) >> 1)));
+        }
+        int n = 0;
+#pragma unroll
+        for (int z = 0; z < S; ++z) {
+          const W la = (W)__shfl_sync(kFull, (unsigned)Lm[z], a);
+          const W fa = (W)__shfl_sync(kFull, (unsigned)fL[z], a);
+          const W lb = (W)__shfl_sync(kFull, (unsigned)Lm[z], b);
+          const W fb = (W)__shfl_sync(kFull, (unsigned)fL[z], b);
+          n += a == b ? popc_w<W>(la & fa) : popc_w<W>(la & fb) + popc_w<W>(lb & fa);
+        }
+        const int ca = __shfl_sync(kFull, (int)cmask, a), cb = __shfl_sync(kFull, (int)cmask, b);
+        const int pa = __shfl_sync(kFull, prank_l, a), pbk = __shfl_sync(kFull, prank_l, b);
+        if (!valid || !ca || !cb) continue;
+        if (!n) {
+          // an empty pair of present levels: its q = p_a p_b enters MI, and
+          // S - u u^T is dense there (-u_a u_b)
+          const long long cc = (long long)ca * cb;
+          mi0 += (a == b ? 1ull : 2ull) * (unsigned long long)cc;
+          const float v = (float)(-cc) * rsqrtf((float)ca * (float)cb) * invT;
+          if (slot) P[pk(kCapL, pa, pbk)] = v;
+          if (fill_s) {
+            Sm[a * mc + b] = v;
+            Sm[b * mc + a] = v;
+          }
+          continue;
+        }
+        const unsigned i = A.lev[a], j = A.lev[b];
+        const int C = (a == b) ? 2 * n : n;
+        const unsigned mult = (a == b) ? 1u : 2u;
+        a1 += (unsigned long long)(mult * (unsigned)C) * (i * j);
+        e2 += (unsigned long long)(mult * (unsigned)C) * (unsigned)C;
+        maxc = max(maxc, (unsigned)C);
+        const float fm = (float)mult;
+        hxy += fm * ent_term(C, T);
+        const long long ct = (long long)C * T, cc = (long long)ca * cb;
+        if (ct != cc)  // p = p_x p_y exactly contributes nothing
+          mi += fm * __fdividef((float)cc, fT2) * kl_term(__fdividef((float)(ct - cc), (float)cc));
+        const float v = (float)(ct - cc) * rsqrtf((float)ca * (float)cb) * invT;
+        if (slot) P[pk(kCapL, pa, pbk)] = v;
+        if (fill_s) {
+          Sm[a * mc + b] = v;
+          Sm[b * mc + a] = v;
+        }
+        atomicAdd(&sbin[i + j - 2 * w.lev0], 2 * n);
+        atomicAdd(&dbin[j - i], 2 * n);
+        if (dbg_glcm) {
+          int32_t* g = dbg_glcm + (size_t)ds * w.ng * w.ng;
+          g[(i - 1) * w.ng + (j - 1)] = C;
+          g[(j - 1) * w.ng + (i - 1)] = C;
+        }
+      }
+    }
+    for (int t0 = 0; S == 0 && t0 < mm2; t0 += 32) {
+      const int t = t0 + lane;
+      if (t >= mm2) continue;
+      const int a = (int)mm.div((unsigned)t), b = t - a * m;
+      if (b < a) continue;
+      const int n = cnt[a * mc + b];
+      if (!n) {
+        const int ca = marg[a], cb = marg[b];
+        if (ca && cb) {
+          // an empty pair of present levels: its q = p_a p_b enters MI, and
+          // S - u u^T is dense there (-u_a u_b)
+          const long long cc = (long long)ca * cb;
+          mi0 += (a == b ? 1ull : 2ull) * (unsigned long long)cc;
+          if (slot)
+            P[pk(kCapL, prank[a], prank[b])] =
+                (float)(-cc) * rsqrtf((float)ca * (float)cb) * invT;
+        }
+        continue;
+      }
+      const unsigned i = A.lev[a], j = A.lev[b];
+      const int C = (a == b) ? 2 * n : n;
+      const unsigned mult = (a == b) ? 1u : 2u;
+      a1 += (unsigned long long)(mult * (unsigned)C) * (i * j);
+      e2 += (unsigned long long)(mult * (unsigned)C) * (unsigned)C;
+      maxc = max(maxc, (unsigned)C);
+      const float fm = (float)mult;
+      hxy += fm * ent_term(C, T);
+      const int ca = marg[a], cb = marg[b];
+      const long long ct = (long long)C * T, cc = (long long)ca * cb;
+      if (ct != cc)  // p = p_x p_y exactly contributes nothing
+        mi += fm * __fdividef((float)cc, fT2) * kl_term(__fdividef((float)(ct - cc), (float)cc));
+      if (clear_now) cnt[a * mc + b] = 0;
+      // A(a', b') = (C T - c_a c_b) / (T sqrt(c_a c_b)) over present ranks
+      if (slot)
+        P[pk(kCapL, prank[a], prank[b])] =
+            (float)(ct - cc) * rsqrtf((float)ca * (float)cb) * invT;
+      atomicAdd(&sbin[i + j - 2 * w.lev0], 2 * n);
+      atomicAdd(&dbin[j - i], 2 * n);
+      if (dbg_glcm) {
+        int32_t* g = dbg_glcm + (size_t)ds * w.ng * w.ng;
+        g[(i - 1) * w.ng + (j - 1)] = C;
+        g[(j - 1) * w.ng + (i - 1)] = C;
+      }
+    }
+    if (merged) {
+      a1 = warp_sum_u64(a1);
+      e2 = warp_sum_u64(e2);
+      mi0 = warp_sum_u64(mi0);
+    } else {  // one direction: each < 2^32
+      a1 = redux_u32((unsigned)a1);
+      e2 = redux_u32((unsigned)e2);
+      mi0 = redux_u32((unsigned)mi0);
+    }
+    maxc = __reduce_max_sync(kFull, maxc);
+    __syncwarp();
+    // MCC: the deflated A = S - u u^T, S = D^-1/2 P D^-1/2 over present levels
+    if (want_mcc) {
+      const int nd = present;
+      if (nd < 2) {
+        if (lane == 0) {
+          mn[ds] = 0;
+          mres[ds] = kNaNf;
+        }
+      } else if (slot) {
+        if (lane == 0) mn[ds] = nd;  // solved after the 13 directions
+      } else {
+        // many levels: warp-cooperative solve now, on S in place of the counts
+        // (the mask path wrote S during its pair rounds)
+        for (int t = lane; S == 0 && t < mm2; t += 32) {
+          const int a = (int)mm.div((unsigned)t), b = t - a * m;
+          if (b < a) continue;
+          const int n = cnt[a * mc + b];
+          const int ca = marg[a], cb = marg[b];
+          float v = 0.f;
+          if (ca && cb) {
+            const int C = (a == b) ? 2 * n : n;
+            const long long num = (long long)C * T - (long long)ca * cb;
+            v = __fdividef((float)num * rsqrtf((float)ca * (float)cb), fT);
+          }
+          Sm[a * mc + b] = v;
+          Sm[b * mc + a] = v;
+        }
+        __syncwarp();
+        const float rho = spectral_radius(Sm, m, mc, vv, ww, dd, ee);
+        if (lane == 0) {
+          mn[ds] = 0;
+          mres[ds] = rho;
+        }
+        __syncwarp();
+        for (int t = lane; t < mm2; t += 32) {
+          const int a = (int)mm.div((unsigned)t);
+          cnt[a * mc + (t - a * m)] = 0;
+        }
+      }
+    }
+    __syncwarp();
+    for (int a = lane; S == 0 && a < m; a += 32) {  // leave the big region zero
+      marg[a] = 0;
+      prank[a] = 0;
+    }
+    // difference and sum distributions (bins relative to the smallest level)
+    unsigned dk = 0, sk = 0;
+    unsigned long long dk2 = 0;
+    float de = 0.f, idm = 0.f, idmn = 0.f, idd = 0.f, idn = 0.f, iv = 0.f, se = 0.f,
+          ce2 = 0.f, ce4 = 0.f;
+    __int128 ce3 = 0;
+    const int nb = 2 * w.R + 1;
+    for (int k = lane; k < nb; k += 32) {
+      if (k <= w.R) {
+        const int c = dbin[k];
+        if (c) {
+          dbin[k] = 0;
+          const float fk = (float)k, fc = (float)c;
+          dk += (unsigned)(k * c);
+          dk2 += (unsigned long long)(k * k) * (unsigned)c;
+          de += ent_term(c, T);
+          idm += __fdividef(fc, 1.f + fk * fk);
+          idmn += __fdividef(fc, 1.f + __fdividef(fk * fk, ngf * ngf));
+          idd += __fdividef(fc, 1.f + fk);
+          idn += __fdividef(fc, 1.f + __fdividef(fk, ngf));
+          if (k) iv += __fdividef(fc, fk * fk);
+        }
+      }
+      const int c = sbin[k];
+      if (c) {
+        sbin[k] = 0;
+        const int kk = k + 2 * w.lev0;
+        sk += (unsigned)(kk * c);
+        se += ent_term(c, T);
+        // T (k - 2 mu): |e| < 2^24 per direction, < 2^26 merged
+        const int e = T * kk - 2 * (int)m1;
+        const float fe = (float)e, fe2 = fe * fe;
+        ce2 += (float)c * fe2;
+        ce4 += (float)c * fe2 * fe2;
+        ce3 += (__int128)((long long)e * e) * ((long long)c * e);
+      }
+    }
+    dk = redux_u32(dk);
+    dk2 = merged ? warp_sum_u64(dk2) : redux_u32((unsigned)dk2);
+    sk = redux_u32(sk);
+    ce3 = warp_sum_i128(ce3);
+    float fs[12] = {hx, hxy, mi, de, idm, idmn, idd, idn, iv, se, ce2, ce4};
+    warp_sum_f32x<12>(fs);
+    fs[2] = (fs[2] + __fdividef((float)mi0, fT2)) * 1.44269504088896341f;  // bits
+    // one lane per feature
+    float num = kNaNf, den = 1.f;
+    const long long var_num = (long long)T * (long long)m2 - (long long)m1 * m1;  // T^2 sigma^2
+    if (lane == 0) { num = (float)a1; den = fT; }
+    if (lane == 1) { num = (float)m1; den = fT; }
+    if (lane == 2) { num = fs[11]; den = fT * fT * fT * fT * fT; }
+    if (lane == 3) {
+      num = i128_to_f32(ce3);
+      den = fT * fT * fT * fT;
+      csn[ds] = i128_to_f64(ce3);
+      cst[ds] = T;
+    }
+    if (lane == 4) { num = fs[10]; den = fT * fT * fT; }
+    if (lane == 5) { num = (float)dk2; den = fT; }
+    if (lane == 6) { num = (float)((long long)T * (long long)a1 - (long long)m1 * m1); den = (float)var_num; }
+    if (lane == 7) { num = (float)dk; den = fT; }
+    if (lane == 8) { num = fs[3]; }
+    if (lane == 9) { num = (float)((long long)T * (long long)dk2 - (long long)dk * dk); den = fT * fT; }
+    if (lane == 10) { num = (float)e2; den = fT * fT; }
+    if (lane == 11) { num = fs[1]; }
+    if (lane == 12) { num = -fs[2]; den = fs[0]; }
+    if (lane == 13) { num = sqrtf(fmaxf(0.f, -expm1f(-2.f * fs[2]))); }
+    if (lane == 14) { num = fs[4]; den = fT; }
+    if (lane == 15) { num = fs[5]; den = fT; }
+    if (lane == 16) { num = fs[6]; den = fT; }
+    if (lane == 17) { num = fs[7]; den = fT; }
+    if (lane == 18) { num = fs[8]; den = fT; }
+    if (lane == 19) { num = (float)maxc; den = fT; }
+    if (lane == 20) { num = (float)sk; den = fT; }
+    if (lane == 21) { num = fs[9]; }
+    if (lane == 22) { num = (float)var_num; den = fT * fT; }
+    acc_lane(A, 23, lane_quot(num, den));
+  }
+  glcm_finish(A, want_mcc, mn, mres, slots, csn, cst);
+}
+
+static __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
+                                   int32_t* dbg_glcm) {
+  if (w.m <= 32 && job.delta == 1 && job.agg != 1) {
+    if (w.s == 3) return glcm_family_impl<3>(w, A, job, dbg_glcm);
+    if (w.s == 5) return glcm_family_impl<5>(w, A, job, dbg_glcm);
+  }
+  glcm_family_impl<0>(w, A, job, dbg_glcm);
+}
+
+// ------------------------------------------------------------------ GLRLM
 // GLRLM of windows of side S <= 5 with at most 32 levels: lane a counts the
 // runs of level a along each direction from its level set: starts are the
 // voxels whose predecessor u - d is not in the set, R_j the voxels that begin
