@@ -620,8 +620,8 @@ __device__ __forceinline__ float rho_reg(const float* __restrict__ P) {
   e2[N - 2] = a[pk(N, N - 2, N - 1)] * a[pk(N, N - 2, N - 1)];
   d[N - 1] = a[pk(N, N - 1, N - 1)];
   e2[N - 1] = 0.f;
-  // Gershgorin bound of the tridiagonal
-  float bnd = 0.f, dmax = d[0], dmin = d[0];
+  // bound on |lambda|: the smaller of the Gershgorin and Frobenius bounds
+  float bnd = 0.f, dmax = d[0], dmin = d[0], fro = 0.f;
   float e[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) e[i] = sqrtf(e2[i]);
@@ -632,8 +632,9 @@ __device__ __forceinline__ float rho_reg(const float* __restrict__ P) {
     bnd = fmaxf(bnd, r);
     dmax = fmaxf(dmax, d[i]);
     dmin = fminf(dmin, d[i]);
+    fro = fmaf(d[i], d[i], fmaf(2.f, e2[i], fro));
   }
-  bnd = bnd * 1.0001f + 1e-20f;
+  bnd = fminf(bnd, sqrtf(fro)) * 1.0001f + 1e-20f;
   // A has the eigenvalue 0, so lambda_max >= 0 >= lambda_min and the radius
   // is max(lambda_max, -lambda_min).  Bracket both ends (lambda_max in
   // [max d_i, bnd], lambda_min in [-bnd, min d_i], by interlacing) until the
@@ -664,6 +665,8 @@ __device__ __forceinline__ float rho_reg(const float* __restrict__ P) {
   const float sg = top ? 1.f : -1.f;
   float lo = top ? hl : -lh, hi = top ? hh : -ll;
   for (; it < kRounds; ++it) {
+    // the bracket is fine enough: half-width <= max(5e-7, 1e-5 lambda)
+    if (hi - lo <= fmaxf(1e-6f, 2e-5f * lo)) break;
     float t[3];
     int c[3];
     const float st = 0.25f * (hi - lo);
