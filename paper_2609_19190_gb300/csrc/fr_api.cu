@@ -340,6 +340,8 @@ struct Engine {
   char* slab = nullptr;
   int64_t slab_stride = 0;
   int slab_ngc = 0;
+  float* fb = nullptr;  // many-level MCC matrices handed to the CTA pool
+  int64_t fb_stride = 0;
   FrArena arena{};
   fr_tune tune{};
   int nw = 0, stages = 0, tile_bytes = 0, smem = 0, grid = 0;
@@ -366,6 +368,8 @@ struct Engine {
     cudaFree(queue);
     cudaFree(status);
     cudaFree(slab);
+    cudaFree(fb);
+    fb = nullptr;
     gexec = nullptr;
     private_stream = nullptr;
     done = nullptr;
@@ -391,6 +395,8 @@ struct Engine {
     a.slab = slab;
     a.slab_stride = slab_stride;
     a.slab_ngc = slab_ngc;
+    a.fb = fb;
+    a.fb_stride = fb_stride;
     a.arena = arena;
     a.dbg = nullptr;
     a.dbg_stride = 0;
@@ -440,6 +446,8 @@ struct Engine {
       } else {
         slab_stride = 0;
       }
+      fb_stride = (int64_t)kNumDirs * kMCap * kMCap;
+      fb = dev_alloc<float>((size_t)grid * nw * fb_stride, &bytes);
       // device job table with tensor maps
       PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
       if (!enc) throw CudaFail{FR_ERR_CUDA};
@@ -663,6 +671,8 @@ struct fr_server {
   int32_t* status = nullptr;
   char* slab = nullptr;
   int64_t slab_stride = 0;
+  float* fb = nullptr;
+  int64_t fb_stride = 0;
   int slab_ngc = 255;
   cudaStream_t stream = nullptr;       // steps
   cudaStream_t plan_stream = nullptr;  // request planning
@@ -695,6 +705,7 @@ void server_release_all(fr_server* S) {
   cudaFree(S->queue);
   cudaFree(S->status);
   cudaFree(S->slab);
+  cudaFree(S->fb);
   cudaFree(S->prep_queue);
   cudaFree(S->prep_status);
   if (S->stream) cudaStreamDestroy(S->stream);
@@ -1243,6 +1254,8 @@ fr_status fr_server_create(int32_t device, int32_t max_radius, int32_t max_slots
     S->slab_stride = fr_align(fr_big_layout(S->slab_ngc, S->slab_ngc, S->arena.w_max).bytes, 256);
     S->slab = dev_alloc<char>((size_t)S->grid * S->nw * S->slab_stride, &S->bytes);
     FR_TRY(cudaMemsetAsync(S->slab, 0, (size_t)S->grid * S->nw * S->slab_stride, S->stream));
+    S->fb_stride = (int64_t)kNumDirs * kMCap * kMCap;
+    S->fb = dev_alloc<float>((size_t)S->grid * S->nw * S->fb_stride, &S->bytes);
     S->jobs_dev = dev_alloc<FrJob>(max_slots, &S->bytes);
     S->run_ptrs_dev = dev_alloc<void*>(2 * (size_t)max_slots, &S->bytes);
     S->max_items = 1 << 16;
@@ -1407,6 +1420,8 @@ fr_status fr_server_step(fr_server* S, int64_t voxel_budget, int32_t* n_active) 
   a.slab = S->slab;
   a.slab_stride = S->slab_stride;
   a.slab_ngc = S->slab_ngc;
+  a.fb = S->fb;
+  a.fb_stride = S->fb_stride;
   a.arena = S->arena;
   a.timeout_ns = kTimeoutNs;
   const int grid = std::min(S->grid, a.n_items);

@@ -22,6 +22,8 @@ constexpr int kCapL = 12;
 constexpr int kSlot = kCapL * (kCapL + 1) / 2 + 1;  // odd: lanes hit distinct banks
 constexpr int kMaxConsumerWarps = 16;
 constexpr int kMaxStages = 4;
+// CTA pool of many-level MCC solves: at most one per direction per warp
+constexpr int kFbTasks = kMaxConsumerWarps * kNumDirs;
 
 // Feature families (bits of FrJob::families).
 enum : uint32_t {
@@ -102,6 +104,8 @@ struct FrMapArgs {
   int64_t slab_stride; // bytes per warp
   int32_t slab_ngc;    // level cap the slab is laid out for
   FrArena arena;
+  float* fb;           // per-warp matrices of many-level MCC solves (kNumDirs x
+  int64_t fb_stride;   // kMCap^2 floats each) handed to the CTA's pool; null: inline
   int32_t* dbg;        // debug records (DUMP kernel only)
   int64_t dbg_stride;  // int32 per record
   int64_t timeout_ns;  // bound of every device wait

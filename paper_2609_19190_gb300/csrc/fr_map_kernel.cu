@@ -23,7 +23,7 @@ constexpr int kStatusUnsupported = 7;  // FR_ERR_UNSUPPORTED
 
 // Shared-memory layout of a CTA (host and device agree through this).
 struct CtaLayout {
-  int32_t tiles, bars, slots, arenas, bytes;
+  int32_t tiles, bars, slots, fb, arenas, bytes;
 };
 
 __host__ __device__ inline CtaLayout fr_cta_layout(int stages, int tile_bytes,
@@ -32,7 +32,8 @@ __host__ __device__ inline CtaLayout fr_cta_layout(int stages, int tile_bytes,
   c.tiles = 0;
   c.bars = stages * tile_bytes;
   c.slots = c.bars + 2 * stages * 8;
-  c.arenas = fr_align(c.slots + stages * 4, 128);
+  c.fb = c.slots + stages * 4;  // pool: count, next, kFbTasks tasks
+  c.arenas = fr_align(c.fb + (2 + kFbTasks) * 4, 128);
   c.bytes = c.arenas + nw * arena_bytes;
   return c;
 }
@@ -112,7 +113,8 @@ template <bool DUMP>
 __device__ void map_voxel(const FrMapArgs& args, const FrJob& job,
                           const FrItem& item, const uint32_t* tile, int t, bool has,
                           Arena& A, char* smem_big, char* slab_big, int it, int nt,
-                          Feeder& fd, bool refill, int stage, unsigned parity) {
+                          Feeder& fd, bool refill, int stage, unsigned parity,
+                          const FbPool& pool, unsigned char* arenas) {
   const int lane = lane_id();
   Win w;
   int col = 0;
@@ -181,7 +183,21 @@ __device__ void map_voxel(const FrMapArgs& args, const FrJob& job,
   consumer_bar(nt);
   if (refill && threadIdx.x == 0) feed(args, fd, stage, parity);
   if (job.families & kFamGLCM) {
-    if (work) glcm_family(w, A, job, d_glcm);
+    const bool use_pool = args.fb != nullptr && (job.families & kFamMCC) != 0;
+    if (work) glcm_family(w, A, job, d_glcm, use_pool ? &pool : nullptr);
+    if (use_pool) {
+      consumer_bar(nt);  // the task list is complete
+      if (*(volatile int*)pool.count > 0) {
+        const int s = 2 * job.r + 1;
+        fb_pool_work(pool, args, s * s * s, arenas, args.arena.bytes, args.arena.off_big, smem_big);
+        consumer_bar(nt);  // every radius is in its owner's results
+        if (threadIdx.x == 0) {
+          *pool.count = 0;
+          *pool.next = 0;
+        }
+      }
+    }
+    if (work) glcm_finish(A, job);
     consumer_bar(nt);
   }
   if (job.families & kFamGLRLM) {
@@ -228,6 +244,9 @@ __global__ void __launch_bounds__(32 * kMaxConsumerWarps, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&fd.full[s], 1);
     fence_mbar_init();
+    int* fbc = (int*)(smem + cl.fb);
+    fbc[0] = 0;
+    fbc[1] = 0;
   }
   // zero this warp's arena (the count matrices must start at zero)
   {
@@ -254,6 +273,12 @@ __global__ void __launch_bounds__(32 * kMaxConsumerWarps, 1)
   char* slab_big = args.slab ? args.slab + ((size_t)blockIdx.x * NW + warp) * args.slab_stride
                              : nullptr;
   const int nt = 32 * NW;
+  FbPool pool;
+  pool.count = (int*)(smem + cl.fb);
+  pool.next = pool.count + 1;
+  pool.tasks = pool.count + 2;
+  pool.scratch = args.fb ? args.fb + ((size_t)blockIdx.x * NW + warp) * args.fb_stride : nullptr;
+  pool.warp = warp;
   int stage = 0;
   unsigned phase = 0;
   while (true) {
@@ -280,7 +305,7 @@ __global__ void __launch_bounds__(32 * kMaxConsumerWarps, 1)
     for (int r = 0; r < rounds; ++r) {
       const int t = r * NW + warp;
       map_voxel<DUMP>(args, job, item, tile, t, t < item.n, A, smem_big, slab_big, it, nt, fd,
-                      r == rounds - 1, stage, phase ^ 1u);
+                      r == rounds - 1, stage, phase ^ 1u, pool, smem + cl.arenas);
     }
     if (++stage == S) {
       stage = 0;

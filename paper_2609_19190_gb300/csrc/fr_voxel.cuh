@@ -787,11 +787,29 @@ __device__ __forceinline__ float kl_term(float d) {
 }
 
 // ------------------------------------------------------------------ GLCM
+// The CTA's pool of many-level MCC solves (more than kCapL present levels):
+// a warp that meets one writes S - u u^T to its global scratch and lists the
+// task; after the GLCM family every warp of the CTA takes tasks from the list
+// and writes the radius into the owner's results, so one voxel's many-level
+// directions no longer hold the whole CTA at the next barrier.
+struct FbPool {
+  int* count;        // tasks listed this round
+  int* next;         // next task to take
+  int* tasks;        // owner warp << 16 | direction << 8 | size
+  float* scratch;    // this warp's matrices, kNumDirs x kMCap^2
+  int warp;
+};
+
 // After the 13 directions: the deferred MCC solves (one lane per direction),
 // the direction means, and ClusterShade's FP64 mean.
-static __device__ void glcm_finish(const Arena& A, bool want_mcc, int* mn, float* mres,
-                                   float* slots, double* csn, int* cst) {
+static __device__ void glcm_finish(const Arena& A, const FrJob& job) {
   const int lane = lane_id();
+  const bool want_mcc = (job.families & kFamMCC) != 0;
+  int* mn = (int*)(A.big + A.L.mn);
+  float* mres = (float*)(A.big + A.L.mres);
+  float* slots = (float*)(A.big + A.L.slots);
+  double* csn = (double*)(A.big + A.L.csn);
+  int* cst = (int*)(A.big + A.L.cst);
   __syncwarp();
   if (want_mcc) {
     // one register-resident size for the warp: the smallest that holds every
@@ -843,7 +861,7 @@ static __device__ void glcm_finish(const Arena& A, bool want_mcc, int* mn, float
 // shared-memory matrix of compact levels.
 template <int S>
 static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJob& job,
-                                        int32_t* dbg_glcm) {
+                                        int32_t* dbg_glcm, const FbPool* pool) {
   const int lane = lane_id();
   const int m = w.m, mc = A.mc;
   int* cnt = (int*)(A.big + A.L.cnt);
@@ -985,7 +1003,13 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
     // mask path, many levels: the pair lanes write S - u u^T for the
     // warp-cooperative solve into the (zero) count region
     const bool fill_s = S > 0 && want_mcc && present > kCapL;
-    float* Sm = (float*)cnt;
+    const bool pooled = pool != nullptr && want_mcc && present > kCapL;
+    float* Sm = pooled ? pool->scratch + (size_t)ds * kMCap * kMCap : (float*)cnt;
+    if (fill_s && pooled)  // the pair lanes write only present pairs
+      for (int t = lane; t < mm2; t += 32) {
+        const int a = (int)mm.div((unsigned)t);
+        Sm[a * mc + (t - a * m)] = 0.f;
+      }
     float* P = slots + ds * kSlot;
     const float invT = __fdividef(1.f, fT);
     if (slot)
@@ -1149,10 +1173,19 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
           Sm[b * mc + a] = v;
         }
         __syncwarp();
-        const float rho = spectral_radius(Sm, m, mc, vv, ww, dd, ee);
-        if (lane == 0) {
-          mn[ds] = 0;
-          mres[ds] = rho;
+        if (pooled) {
+          if (lane == 0) {
+            mn[ds] = 0;
+            mres[ds] = kNaNf;  // the pool writes the radius
+            const int slot_i = atomicAdd(pool->count, 1);
+            pool->tasks[slot_i] = (pool->warp << 16) | (ds << 8) | m;
+          }
+        } else {
+          const float rho = spectral_radius(Sm, m, mc, vv, ww, dd, ee);
+          if (lane == 0) {
+            mn[ds] = 0;
+            mres[ds] = rho;
+          }
         }
         __syncwarp();
         for (int t = lane; t < mm2; t += 32) {
@@ -1243,16 +1276,58 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
     if (lane == 22) { num = (float)var_num; den = fT * fT; }
     acc_lane(A, 23, lane_quot(num, den));
   }
-  glcm_finish(A, want_mcc, mn, mres, slots, csn, cst);
 }
 
-static __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
-                                   int32_t* dbg_glcm) {
-  if (w.m <= 32 && job.delta == 1 && job.agg != 1) {
-    if (w.s == 3) return glcm_family_impl<3>(w, A, job, dbg_glcm);
-    if (w.s == 5) return glcm_family_impl<5>(w, A, job, dbg_glcm);
+// One warp's share of the CTA pool: take listed tasks until none is left;
+// each copies the owner's matrix into this warp's shared-memory region, solves
+// it there, clears it, and stores the radius in the owner's results.  Every
+// consumer warp calls this between two CTA barriers (the list is complete).
+static __device__ void fb_pool_work(const FbPool& P, const FrMapArgs& args, int W,
+                                    unsigned char* arenas, int arena_bytes, int arena_off_big,
+                                    char* my_big) {
+  const int lane = lane_id();
+  const BigLayout L = fr_big_layout(kMCap, kBinCap, W);
+  const int count = *(volatile int*)P.count;
+  float* S = (float*)my_big;  // this warp's count region (zero on entry and exit)
+  float* vv = (float*)(my_big + L.vec);
+  while (true) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(P.next, 1);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= count) break;
+    const int task = P.tasks[t];
+    const int owner = task >> 16, d = (task >> 8) & 0xFF, n = task & 0xFF;
+    const float* src = args.fb + ((size_t)blockIdx.x * args.consumer_warps + owner) * args.fb_stride +
+                       (size_t)d * kMCap * kMCap;
+    for (int e = lane; e < n * n; e += 32) {
+      const int a = e / n, b = e - a * n;
+      S[a * kMCap + b] = src[a * kMCap + b];
+    }
+    __syncwarp();
+    const float rho = spectral_radius(S, n, kMCap, vv, vv + kMCap, vv + 2 * kMCap, vv + 3 * kMCap);
+    __syncwarp();
+    for (int e = lane; e < n * n; e += 32) {
+      const int a = e / n, b = e - a * n;
+      S[a * kMCap + b] = 0.f;
+    }
+    if (lane == 0) {
+      float* mres = (float*)(arenas + (size_t)owner * arena_bytes + arena_off_big + L.mres);
+      mres[d] = rho;
+    }
+    __syncwarp();
   }
-  glcm_family_impl<0>(w, A, job, dbg_glcm);
+}
+
+// pool: many-level MCC solves go to the CTA pool (windows in shared memory);
+// null solves them inline.  The caller runs glcm_finish after the pool.
+static __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
+                                   int32_t* dbg_glcm, const FbPool* pool) {
+  if (A.mc != kMCap) pool = nullptr;
+  if (w.m <= 32 && job.delta == 1 && job.agg != 1) {
+    if (w.s == 3) return glcm_family_impl<3>(w, A, job, dbg_glcm, pool);
+    if (w.s == 5) return glcm_family_impl<5>(w, A, job, dbg_glcm, pool);
+  }
+  glcm_family_impl<0>(w, A, job, dbg_glcm, pool);
 }
 
 // ------------------------------------------------------------------ GLRLM
