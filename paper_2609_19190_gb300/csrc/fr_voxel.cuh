@@ -1042,10 +1042,10 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
         int n = 0;
 #pragma unroll
         for (int z = 0; z < S; ++z) {
-          const W la = (W)__shfl_sync(kFull, (unsigned)Lm[z], a);
-          const W fa = (W)__shfl_sync(kFull, (unsigned)fL[z], a);
-          const W lb = (W)__shfl_sync(kFull, (unsigned)Lm[z], b);
-          const W fb = (W)__shfl_sync(kFull, (unsigned)fL[z], b);
+          const W la = __shfl_sync(kFull, Lm[z], a);
+          const W fa = __shfl_sync(kFull, fL[z], a);
+          const W lb = __shfl_sync(kFull, Lm[z], b);
+          const W fb = __shfl_sync(kFull, fL[z], b);
           n += a == b ? popc_w<W>(la & fa) : popc_w<W>(la & fb) + popc_w<W>(lb & fa);
         }
         const int ca = __shfl_sync(kFull, (int)cmask, a), cb = __shfl_sync(kFull, (int)cmask, b);
@@ -1326,6 +1326,7 @@ static __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& jo
   if (w.m <= 32 && job.delta == 1 && job.agg != 1) {
     if (w.s == 3) return glcm_family_impl<3>(w, A, job, dbg_glcm, pool);
     if (w.s == 5) return glcm_family_impl<5>(w, A, job, dbg_glcm, pool);
+    if (w.s == 7) return glcm_family_impl<7>(w, A, job, dbg_glcm, pool);
   }
   glcm_family_impl<0>(w, A, job, dbg_glcm, pool);
 }
