@@ -52,3 +52,34 @@ def test_tiny_full_size_all_columns():
     got, plan, feats = H.gpu_map(img, mask, disc_mode=0, bin_count=16, kernel_radius=1)
     ref, _, _, _ = H.oracle_map(img, mask, disc_mode=0, bin_count=16, kernel_radius=1)
     parity.assert_close(got, ref[feats], [O.feature_names()[f] for f in feats])
+
+
+def test_batched_workload_items_against_oracle_sampled():
+    # the first 6 requests of the batched workload (128x128x64 CT-like volumes,
+    # log-uniform VOI sizes, r in {1,2,3}, FBN 16/32/64), one batched launch,
+    # each VOI checked on 200 seeded voxels against the oracle
+    import torch
+
+    import paper_2609_19190_gb300 as fm
+    params, masks, imgs, host, kws = [], [], [], [], []
+    for i in range(6):
+        img, mask, r, bins = synth.batch_item(i)
+        kw = dict(disc_mode=0, bin_count=bins, kernel_radius=r)
+        nz, ny, nx = img.shape
+        params.append(fm.fr_map_params_init(nx, ny, nz, **kw))
+        masks.append(torch.from_numpy(mask))
+        imgs.append(torch.from_numpy(img).cuda())
+        host.append((img, mask))
+        kws.append(kw)
+    b = fm.fr_batch_plan(params, masks)
+    outs = fm.fr_batch_run(b, imgs)
+    fm.fr_batch_sync_status(b)
+    names = O.feature_names()
+    for (img, mask), kw, out in zip(host, kws, outs):
+        allvox = np.flatnonzero(mask.reshape(-1))
+        vox = synth.sample_voxels(mask, 200, 31)
+        ref, _, _, _ = H.oracle_map(img, mask, voxels=vox, **kw)
+        cols = np.searchsorted(allvox, vox)
+        got = out.cpu().numpy().astype(np.float64)[:, cols]
+        parity.assert_close(got, ref, names)
+    fm.fr_batch_destroy(b)

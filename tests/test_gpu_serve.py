@@ -44,6 +44,19 @@ def test_served_results_equal_alone_and_in_the_mix():
         got = stats["outputs"][i]
         assert torch.equal(got.view(torch.int32), ref.view(torch.int32)), i
     assert stats["p50_s"] <= stats["p99_s"]
+    # and against the oracle on seeded voxels of two requests
+    import gpu_helpers as H
+    import parity
+    from oracle import oracle as O
+    for i in (0, len(reqs) - 1):
+        rq = reqs[i]
+        img = imgs[rq["shape"]].cpu().numpy()
+        mask = rq["mask"]
+        vox = synth.sample_voxels(mask, 100, 17)
+        cols = np.searchsorted(np.flatnonzero(mask.reshape(-1)), vox)
+        ref, _, _, _ = H.oracle_map(img, mask, voxels=vox, kernel_radius=rq["radius"], **rq["disc"])
+        got = stats["outputs"][i].cpu().numpy().astype(np.float64)[:, cols]
+        parity.assert_close(got, ref, O.feature_names())
 
 
 def test_late_small_request_overtakes_a_large_one():
