@@ -79,7 +79,13 @@ const char* const kNames[FRO_NUM_FEATURES] = {
     "gldm_LargeDependenceHighGrayLevelEmphasis",
     /* NGTDM (5) */
     "ngtdm_Coarseness", "ngtdm_Contrast", "ngtdm_Busyness", "ngtdm_Complexity",
-    "ngtdm_Strength"};
+    "ngtdm_Strength",
+    /* IBSI extras completing the 101-map default set (ids 93..100) */
+    "firstorder_MedianAbsoluteDeviation", "firstorder_CoefficientOfVariation",
+    "firstorder_QuartileCoefficientOfDispersion", "glcm_SumVariance",
+    "glcm_Dissimilarity", "gldm_GrayLevelNonUniformityNormalized",
+    "gldm_DependencePercentage", "gldm_DependenceEnergy"
+};
 
 /* The 13 directions of 3-D texture analysis: one vector d of every +-d pair
  * of the 26-neighbourhood, taken as the vectors (dz, dy, dx) that are
@@ -641,6 +647,88 @@ void gldm_features(const std::vector<double>& M, int ng, int nj, double* f) {
   f[13] = ldh;
 }
 
+/* IBSI statistics beyond the benchmark set, raw intensities x:
+ * median absolute deviation (1/N) sum |x - median|, coefficient of variation
+ * sigma / mean (population sigma; NaN for a zero mean), quartile coefficient
+ * of dispersion (P75 - P25) / (P75 + P25) (NaN for a zero denominator), with
+ * the percentiles of firstorder_features. */
+void firstorder_extra(std::vector<int> x, double* f) {
+  const int64_t n = (int64_t)x.size();
+  if (n == 0) {
+    for (int k = 0; k < 3; ++k) f[k] = kNaN;
+    return;
+  }
+  std::sort(x.begin(), x.end());
+  auto pct = [&](int q) {
+    const int64_t num = (n - 1) * q, k = num / 100, rem = num % 100;
+    if (rem == 0) return (double)x[k];
+    return x[k] + (rem / 100.0) * (double)(x[k + 1] - x[k]);
+  };
+  const double N = (double)n, med = pct(50);
+  double sum = 0, medad = 0;
+  for (int v : x) {
+    sum += v;
+    medad += std::fabs(v - med);
+  }
+  const double mean = sum / N;
+  double m2 = 0;
+  for (int v : x) m2 += (v - mean) * (v - mean);
+  m2 /= N;
+  const double p25 = pct(25), p75 = pct(75);
+  f[0] = medad / N;
+  f[1] = safe_div(std::sqrt(m2), mean);
+  f[2] = safe_div(p75 - p25, p75 + p25);
+}
+
+/* GLCM sum variance sum_k (k - SA)^2 p_{x+y}(k), SA = sum_k k p_{x+y}(k), and
+ * dissimilarity sum_k k p_{x-y}(k) (IBSI) of one symmetric count matrix. */
+void glcm_extra(const std::vector<double>& C, int ng, double* f) {
+  double T = 0.0;
+  for (double v : C) T += v;
+  if (T == 0.0) {
+    f[0] = f[1] = kNaN;
+    return;
+  }
+  std::vector<double> pxpy(2 * ng + 1, 0.0), pxmy(ng, 0.0);
+  for (int i = 1; i <= ng; ++i)
+    for (int j = 1; j <= ng; ++j) {
+      const double p = C[(size_t)(i - 1) * ng + (j - 1)] / T;
+      pxpy[i + j] += p;
+      pxmy[std::abs(i - j)] += p;
+    }
+  double sa = 0, sv = 0, dis = 0;
+  for (int k = 2; k <= 2 * ng; ++k) sa += k * pxpy[k];
+  for (int k = 2; k <= 2 * ng; ++k) sv += (k - sa) * (k - sa) * pxpy[k];
+  for (int k = 0; k < ng; ++k) dis += k * pxmy[k];
+  f[0] = sv;
+  f[1] = dis;
+}
+
+/* NGLDM extras (IBSI) of a dependence count matrix [ng][nj]: grey level
+ * non-uniformity normalised sum_i (sum_j s_ij)^2 / N_s^2, dependence count
+ * percentage N_s / N_v, dependence count energy sum_ij p_ij^2. */
+void gldm_extra(const std::vector<double>& M, int ng, int nj, double nv, double* f) {
+  double N = 0;
+  for (double v : M) N += v;
+  if (N == 0) {
+    for (int k = 0; k < 3; ++k) f[k] = kNaN;
+    return;
+  }
+  double glnu = 0, energy = 0;
+  for (int i = 0; i < ng; ++i) {
+    double row = 0;
+    for (int j = 0; j < nj; ++j) {
+      const double p = M[(size_t)i * nj + j] / N;
+      row += M[(size_t)i * nj + j];
+      energy += p * p;
+    }
+    glnu += row * row;
+  }
+  f[0] = glnu / (N * N);
+  f[1] = N / nv;
+  f[2] = energy;
+}
+
 /* NGTDM features (IBSI).  N_vp = sum n_i, p_i = n_i / N_vp, N_gp = number of
  * levels with p_i > 0; sums over i, j run over those levels.
  * Undefined values: N_vp = 0 -> all NaN; a zero denominator -> NaN, except
@@ -821,8 +909,9 @@ void map_one(const fro_params* p, const Cube& c, int ng, double* f) {
   const double nv = (double)x.size();
   const double vvox = p->spacing[0] * p->spacing[1] * p->spacing[2];
   firstorder_features(x, g, ng, vvox, p->kurtosis_excess, f + 0);
+  firstorder_extra(x, f + 93);
 
-  std::vector<double> M, per((size_t)FRO_NUM_DIRS * 24);
+  std::vector<double> M, per((size_t)FRO_NUM_DIRS * 24), perx((size_t)FRO_NUM_DIRS * 2);
   if (p->aggregation == FRO_AGG_MERGED) {
     /* one matrix: the sum of the 13 directional matrices */
     std::vector<double> sum((size_t)ng * ng, 0.0);
@@ -831,6 +920,7 @@ void map_one(const fro_params* p, const Cube& c, int ng, double* f) {
       for (size_t k = 0; k < sum.size(); ++k) sum[k] += M[k];
     }
     glcm_features(sum, ng, f + 18);
+    glcm_extra(sum, ng, f + 96);
     std::vector<double> rsum((size_t)ng * c.s, 0.0);
     for (int d = 0; d < FRO_NUM_DIRS; ++d) {
       glrlm_counts(c, dirs[d], ng, M);
@@ -841,8 +931,10 @@ void map_one(const fro_params* p, const Cube& c, int ng, double* f) {
     for (int d = 0; d < FRO_NUM_DIRS; ++d) {
       glcm_counts(c, dirs[d], p->distance, ng, M);
       glcm_features(M, ng, &per[(size_t)d * 24]);
+      glcm_extra(M, ng, &perx[(size_t)d * 2]);
     }
     average_dirs(per, FRO_NUM_DIRS, 24, f + 18);
+    average_dirs(perx, FRO_NUM_DIRS, 2, f + 96);
 
     per.assign((size_t)FRO_NUM_DIRS * 16, 0.0);
     for (int d = 0; d < FRO_NUM_DIRS; ++d) {
@@ -858,6 +950,7 @@ void map_one(const fro_params* p, const Cube& c, int ng, double* f) {
 
   gldm_counts(c, ng, M);
   gldm_features(M, ng, 27, f + 74);
+  gldm_extra(M, ng, 27, nv, f + 98);
 
   std::vector<double> n, s;
   ngtdm_counts(c, ng, n, s, nullptr);

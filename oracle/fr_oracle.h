@@ -13,8 +13,14 @@
  * with the image and the VOI, and map_f(v) = feature_f(V(v)).  Gray levels
  * come from one discretisation of the whole VOI (paper: "Hybrid CUDA backend
  * implementation" -- discretisation is a preprocessing step over the VOI).
- * Feature families and counts follow Table 2 (spatial benchmark column:
- * statistics 18, GLCM 24, GLRLM 16, GLSZM 16, NGLDM 14, NGTDM 5 = 93).
+ * Feature families and counts follow Table 2: ids 0..92 are the spatial
+ * benchmark column (statistics 18, GLCM 24, GLRLM 16, GLSZM 16, NGLDM 14,
+ * NGTDM 5 = 93); ids 93..100 complete the default spatial column (101: +3
+ * statistics, +2 GLCM, +3 NGLDM), read as the IBSI features the benchmark's
+ * PyRadiomics-named classes lack: median absolute deviation, coefficient of
+ * variation, quartile coefficient of dispersion; GLCM sum variance and
+ * dissimilarity; NGLDM grey level non-uniformity normalised, dependence
+ * count percentage and dependence count energy.
  * The paper prints no formula; the definitions used are the IBSI ones the
  * paper says both of its backends follow (Introduction; "IBSI compliance
  * tests"), written out in fr_oracle.cpp next to each feature.
@@ -41,7 +47,8 @@ enum { FRO_ANCHOR_VOI_MIN = 0, FRO_ANCHOR_ZERO_FLOOR = 1 };
  * per family).  Merged GLRLM run percentage divides by 13 N_v. */
 enum { FRO_AGG_AVERAGE = 0, FRO_AGG_MERGED = 1 };
 
-#define FRO_NUM_FEATURES 93
+#define FRO_NUM_FEATURES 101
+#define FRO_NUM_BENCH 93
 #define FRO_NUM_DIRS 13
 
 typedef struct fro_params {
@@ -72,18 +79,18 @@ int32_t fro_discretise(const fro_params* p, const int16_t* img,
                        int32_t* xmin, int32_t* xmax);
 
 /* Feature maps at the listed voxels (linear indices (z*ny + y)*nx + x, each
- * inside the VOI).  out is [93][n] (feature-major).  nthreads <= 0 uses the
+ * inside the VOI).  out is [101][n] (feature-major).  nthreads <= 0 uses the
  * OpenMP default.  Returns 0 on success. */
 int32_t fro_map_voxels(const fro_params* p, const int16_t* img,
                        const uint8_t* levels, int32_t ng, const int64_t* vox,
                        int64_t n, double* out, int32_t nthreads);
 
-/* Scalar extraction: the 93 features of the whole VOI (the paper's other
+/* Scalar extraction: the 101 features of the whole VOI (the paper's other
  * extraction mode; the map value at v equals it whenever the window around v
  * covers the VOI).  levels from fro_discretise; p->radius is ignored.
  * Returns 0, 1 for an empty VOI, 3 for invalid parameters. */
 int32_t fro_scalar(const fro_params* p, const int16_t* img, const uint8_t* levels,
-                   int32_t ng, double* out93);
+                   int32_t ng, double* out101);
 
 /* Dense texture matrices of one voxel's sub-VOI V(v) (bit-exact integers).
  * glcm  : [13][ng][ng]  symmetric co-occurrence counts (levels 1..ng at 0..ng-1)

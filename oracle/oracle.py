@@ -11,7 +11,8 @@ import numpy as np
 
 from . import build as _build
 
-NUM_FEATURES = 93
+NUM_FEATURES = 101
+NUM_BENCH = 93  # ids 0..92: the spatial benchmark set
 NUM_DIRS = 13
 FBN, FBW = 0, 1
 ANCHOR_VOI_MIN, ANCHOR_ZERO_FLOOR = 0, 1
@@ -111,7 +112,7 @@ def discretise(params, image, mask):
 
 
 def map_voxels(params, image, levels, ng, voxels, nthreads=0):
-    """Feature maps [93, n] (float64) at the listed linear voxel indices."""
+    """Feature maps [101, n] (float64) at the listed linear voxel indices."""
     image = np.ascontiguousarray(image, dtype=np.int16)
     levels = np.ascontiguousarray(levels, dtype=np.uint8)
     vox = np.ascontiguousarray(voxels, dtype=np.int64)
@@ -126,14 +127,14 @@ def map_voxels(params, image, levels, ng, voxels, nthreads=0):
 def map_volume(params, image, mask, nthreads=0):
     """Discretise and map every VOI voxel (z-major order).
 
-    Returns (maps [93, n_voi], voxel linear indices, levels, Ng)."""
+    Returns (maps [101, n_voi], voxel linear indices, levels, Ng)."""
     levels, ng, _, _ = discretise(params, image, mask)
     vox = np.flatnonzero(np.asarray(mask).reshape(-1)).astype(np.int64)
     return map_voxels(params, image, levels, ng, vox, nthreads), vox, levels, ng
 
 
 def scalar(params, image, levels, ng):
-    """The 93 features of the whole VOI (scalar extraction)."""
+    """The 101 features of the whole VOI (scalar extraction)."""
     image = np.ascontiguousarray(image, dtype=np.int16)
     levels = np.ascontiguousarray(levels, dtype=np.uint8)
     out = np.empty(NUM_FEATURES)

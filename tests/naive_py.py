@@ -294,6 +294,41 @@ def firstorder_features(x, g, ng, vvox=1.0, excess=True):
     return np.array(f, float)
 
 
+def firstorder_extra(x):
+    """IBSI median absolute deviation, coefficient of variation, quartile
+    coefficient of dispersion."""
+    x = np.asarray(x, float)
+    p25, p50, p75 = np.percentile(x, [25, 50, 75])
+    m = x.mean()
+    cov = np.sqrt(x.var()) / m if m != 0 else np.nan
+    qcod = (p75 - p25) / (p75 + p25) if (p75 + p25) != 0 else np.nan
+    return np.array([np.abs(x - p50).mean(), cov, qcod], float)
+
+
+def glcm_extra(C, ng):
+    """IBSI sum variance and dissimilarity of one direction's counts."""
+    C = np.asarray(C, float)
+    T = C.sum()
+    if T == 0:
+        return np.full(2, np.nan)
+    P = C / T
+    i = np.arange(1, ng + 1)[:, None] * np.ones((1, ng))
+    j = i.T
+    ks = (i + j).ravel()
+    kd = np.abs(i - j).ravel()
+    pp = P.ravel()
+    sa = (ks * pp).sum()
+    return np.array([((ks - sa) ** 2 * pp).sum(), (kd * pp).sum()], float)
+
+
+def gldm_extra(M, nv):
+    """IBSI grey level non-uniformity normalised, dependence count percentage,
+    dependence count energy."""
+    M = np.asarray(M, float)
+    N = M.sum()
+    return np.array([(M.sum(1) ** 2).sum() / N ** 2, N / nv, ((M / N) ** 2).sum()], float)
+
+
 def _nanmean_rows(a):
     a = np.asarray(a, float)
     out = np.full(a.shape[1], np.nan)
@@ -306,7 +341,8 @@ def _nanmean_rows(a):
 
 
 def features_of_cube(lv, raw, ng, delta=1, vvox=1.0, excess=True, merged=False):
-    """All 93 features of one sub-VOI cube.  merged: GLCM and GLRLM features
+    """All 101 features of one sub-VOI cube (93 benchmark maps, then the 8
+    IBSI extras).  merged: GLCM and GLRLM features
     of the sum of the 13 directional matrices (run percentage over 13 N_v)."""
     inside = lv > 0
     nv = int(inside.sum())
@@ -315,15 +351,19 @@ def features_of_cube(lv, raw, ng, delta=1, vvox=1.0, excess=True, merged=False):
     R = glrlm(lv, ng)
     if merged:
         gl = glcm_features(G.sum(axis=0), ng)
+        gx = glcm_extra(G.sum(axis=0), ng)
         rl = rl_features(R.sum(axis=0), 13 * nv)
     else:
         gl = _nanmean_rows([glcm_features(G[k], ng) for k in range(13)])
+        gx = _nanmean_rows([glcm_extra(G[k], ng) for k in range(13)])
         rl = _nanmean_rows([rl_features(R[k], nv) for k in range(13)])
     sz = rl_features(glszm(lv, ng), nv)
     dm = gldm_features(gldm(lv, ng))
     n, s = ngtdm_exact(lv, ng)
     nt = ngtdm_features(n, s)
-    return np.concatenate([fo, gl, rl, sz, dm, nt])
+    fx = firstorder_extra(raw[inside])
+    dx = gldm_extra(gldm(lv, ng), nv)
+    return np.concatenate([fo, gl, rl, sz, dm, nt, fx, gx, dx])
 
 
 def map_voxels(levels, image, ng, voxels, r, delta=1, vvox=1.0, excess=True, merged=False):

@@ -393,6 +393,32 @@ def test_ngtdm_constant_and_two_level():
     assert math.isnan(f[2]) and math.isfinite(f[0]) and math.isfinite(f[4])
 
 
+def test_ibsi_extras_closed_forms_and_identities():
+    # ramp 0..10: median 5, median absolute deviation 30/11, CoV sqrt(10)/5,
+    # P25 = 2.5, P75 = 7.5, QCoD = 0.5
+    img = np.arange(11, dtype=np.int16).reshape(1, 1, 11)
+    mask = np.ones_like(img, dtype=np.uint8)
+    p = O.make_params(img.shape, disc_mode=O.FBN, bin_count=4)
+    lev, ng, _, _ = O.discretise(p, img, mask)
+    f = O.scalar(p, img, lev, ng)
+    assert f[93] == pytest.approx(30 / 11, rel=1e-14)
+    assert f[94] == pytest.approx(math.sqrt(10) / 5, rel=1e-14)
+    assert f[95] == pytest.approx(0.5, rel=1e-14)
+    # on random windows: sum variance = cluster tendency and dissimilarity =
+    # difference average (identities of a symmetric GLCM), dependence count
+    # percentage = 1 (every voxel has a dependence count), GLNUN = GLNU / N_v
+    rng = np.random.default_rng(52)
+    img = rng.integers(0, 70, size=(7, 7, 7)).astype(np.int16)
+    mask = (rng.random(img.shape) < 0.7).astype(np.uint8)
+    maps, vox, levels, ng = _oracle_maps(img, mask, disc_mode=O.FBN, bin_count=6, radius=2)
+    nv = np.array([O.matrices(O.make_params(img.shape, disc_mode=O.FBN, bin_count=6, radius=2),
+                              levels, ng, v)["hist"].sum() for v in vox])
+    np.testing.assert_allclose(maps[96], maps[22], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(maps[97], maps[25], rtol=1e-12, atol=1e-14)
+    np.testing.assert_array_equal(maps[99], np.ones(len(vox)))
+    np.testing.assert_allclose(maps[98], maps[76] / nv, rtol=1e-12)
+
+
 def test_firstorder_closed_form_ramp():
     n = 11
     x = np.arange(n)
@@ -500,7 +526,8 @@ def test_merged_linear_features_are_weighted_direction_means():
         assert mrg[48, k] == pytest.approx(avg[48, k], rel=1e-12)
     # families without a direction are the same in both modes
     np.testing.assert_array_equal(mrg[:18], avg[:18])
-    np.testing.assert_array_equal(mrg[58:], avg[58:])
+    np.testing.assert_array_equal(mrg[58:96], avg[58:96])
+    np.testing.assert_array_equal(mrg[98:], avg[98:])
 
 
 @pytest.mark.parametrize("kw", [dict(disc_mode=O.FBN, bin_count=6),
@@ -542,16 +569,16 @@ def test_map_flip_permutation_translation_equivariance():
     mask = (rng.random(img.shape) < 0.7).astype(np.uint8)
     kw = dict(disc_mode=O.FBN, bin_count=6, radius=1)
     base, vox, _, _ = _oracle_maps(img, mask, **kw)
-    base_vol = np.full((93,) + img.shape, np.nan)
-    base_vol.reshape(93, -1)[:, vox] = base
+    base_vol = np.full((O.NUM_FEATURES,) + img.shape, np.nan)
+    base_vol.reshape(O.NUM_FEATURES, -1)[:, vox] = base
     for transform in (lambda a: a[::-1], lambda a: a[:, ::-1], lambda a: a[:, :, ::-1],
                       lambda a: np.transpose(a, (2, 0, 1)), lambda a: np.transpose(a, (1, 2, 0))):
         t_img = np.ascontiguousarray(transform(img))
         t_mask = np.ascontiguousarray(transform(mask))
         got, t_vox, _, _ = _oracle_maps(t_img, t_mask, **kw)
-        vol = np.full((93,) + t_img.shape, np.nan)
-        vol.reshape(93, -1)[:, t_vox] = got
-        expect = np.stack([np.ascontiguousarray(transform(base_vol[f])) for f in range(93)])
+        vol = np.full((O.NUM_FEATURES,) + t_img.shape, np.nan)
+        vol.reshape(O.NUM_FEATURES, -1)[:, t_vox] = got
+        expect = np.stack([np.ascontiguousarray(transform(base_vol[f])) for f in range(O.NUM_FEATURES)])
         np.testing.assert_allclose(vol, expect, rtol=1e-9, atol=1e-9, equal_nan=True)
     # translation: zero padding outside the mask changes nothing
     pad_img = np.pad(img, 3, constant_values=0)
@@ -560,11 +587,15 @@ def test_map_flip_permutation_translation_equivariance():
     np.testing.assert_allclose(got, base, rtol=0, atol=0, equal_nan=True)
 
 
-def test_feature_names_are_the_93_benchmark_maps():
+def test_feature_names_are_the_101_default_maps():
+    # Table 2: the 93-map benchmark column first, then the 8 maps that complete
+    # the 101-map default column (+3 statistics, +2 GLCM, +3 NGLDM)
     n = names()
-    assert len(n) == 93 and len(set(n)) == 93
+    assert len(n) == 101 and len(set(n)) == 101
     fam = [k.split("_")[0] for k in n]
-    assert [fam.count(f) for f in ("firstorder", "glcm", "glrlm", "glszm", "gldm", "ngtdm")] == \
+    assert [fam[:93].count(f) for f in ("firstorder", "glcm", "glrlm", "glszm", "gldm", "ngtdm")] == \
         [18, 24, 16, 16, 14, 5]
+    assert [fam.count(f) for f in ("firstorder", "glcm", "glrlm", "glszm", "gldm", "ngtdm")] == \
+        [21, 26, 16, 16, 17, 5]
     assert sorted(O.directions()) == sorted(
         d for d in itertools.product((-1, 0, 1), repeat=3) if d > (0, 0, 0))
