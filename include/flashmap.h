@@ -73,12 +73,21 @@ enum { FR_ANCHOR_VOI_MIN = 0, FR_ANCHOR_ZERO_FLOOR = 1 };    /* FBW bin anchor  
  * voxel lies on one run per direction).  GLSZM, GLDM and NGTDM do not
  * depend on a direction. */
 enum { FR_AGG_AVERAGE = 0, FR_AGG_MERGED = 1 };
-enum { FR_NUM_FEATURES = 93, FR_NUM_DIRECTIONS = 13, FR_MAX_RADIUS = 7 };
+/* 101 features (Table 2's default spatial column): ids 0..92 are the 93-map
+ * benchmark set, ids 93..100 the IBSI features completing the default set
+ * (see FR_EXTRAS_BEGIN).  fr_map_params_init selects the 93 benchmark maps. */
+enum { FR_NUM_FEATURES = 101, FR_NUM_BENCH_FEATURES = 93, FR_NUM_DIRECTIONS = 13,
+       FR_MAX_RADIUS = 7 };
 
 /* Feature id ranges (ids are stable; names from fr_feature_name). */
 enum {
   FR_FIRSTORDER_BEGIN = 0, FR_GLCM_BEGIN = 18, FR_GLRLM_BEGIN = 42,
-  FR_GLSZM_BEGIN = 58, FR_GLDM_BEGIN = 74, FR_NGTDM_BEGIN = 88, FR_FEATURES_END = 93
+  FR_GLSZM_BEGIN = 58, FR_GLDM_BEGIN = 74, FR_NGTDM_BEGIN = 88,
+  /* 93..95 statistics: median absolute deviation, coefficient of variation,
+   * quartile coefficient of dispersion; 96..97 GLCM: sum variance,
+   * dissimilarity; 98..100 NGLDM: grey level non-uniformity normalised,
+   * dependence count percentage, dependence count energy (IBSI) */
+  FR_EXTRAS_BEGIN = 93, FR_FEATURES_END = 101
 };
 
 /* Mapping parameters (the paper's settings object: feature families,

@@ -34,6 +34,8 @@ __all__ = [
 FAMILIES = {
     "firstorder": range(0, 18), "glcm": range(18, 42), "glrlm": range(42, 58),
     "glszm": range(58, 74), "gldm": range(74, 88), "ngtdm": range(88, 93),
+    # IBSI extras completing Table 2's 101-map default set
+    "extras": range(93, 101),
 }
 
 

@@ -17,7 +17,8 @@ STATUS_NAMES = {
 
 FR_FBN, FR_FBW = 0, 1
 FR_ANCHOR_VOI_MIN, FR_ANCHOR_ZERO_FLOOR = 0, 1
-FR_NUM_FEATURES = 93
+FR_NUM_FEATURES = 101
+FR_NUM_BENCH_FEATURES = 93  # ids 0..92: the benchmark maps (the default selection)
 FR_NUM_DIRECTIONS = 13
 
 

@@ -29,7 +29,7 @@ def _families(features):
     fam = 0
     for f in features:
         fam |= 1 << (0 if f < 18 else 1 if f < 42 else 2 if f < 58 else 3 if f < 74 else
-                     4 if f < 88 else 5)
+                     4 if f < 88 else 5 if f < 93 else 0 if f < 96 else 1 if f < 98 else 4)
     return fam
 
 

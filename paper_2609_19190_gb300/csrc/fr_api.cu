@@ -94,7 +94,13 @@ const char* const kFeatureNames[kNumFeatures] = {
     "gldm_LargeDependenceLowGrayLevelEmphasis",
     "gldm_LargeDependenceHighGrayLevelEmphasis",
     "ngtdm_Coarseness", "ngtdm_Contrast", "ngtdm_Busyness", "ngtdm_Complexity",
-    "ngtdm_Strength"};
+    "ngtdm_Strength",
+    // IBSI extras completing the 101-map default set
+    "firstorder_MedianAbsoluteDeviation", "firstorder_CoefficientOfVariation",
+    "firstorder_QuartileCoefficientOfDispersion", "glcm_SumVariance", "glcm_Dissimilarity",
+    "gldm_GrayLevelNonUniformityNormalized", "gldm_DependencePercentage",
+    "gldm_DependenceEnergy"
+};
 
 // Directions (dz, dy, dx) in the documented order.
 const int kDirs[kNumDirs][3] = {{0, 0, 1},  {0, 1, -1}, {0, 1, 0},  {0, 1, 1},
@@ -199,7 +205,7 @@ struct JobRes {
   fr_map_params p;
   int64_t n_voi = 0;
   int32_t nf = 0;
-  int16_t row_of[96];
+  int16_t row_of[kRowOf];
   uint32_t families = 0;
   int32_t px = 0;
   int32_t ngc = 0;  // level cap of this job
@@ -233,9 +239,11 @@ void select_features(JobRes& j) {
     if (f >= FR_GLRLM_BEGIN && f < FR_GLSZM_BEGIN) j.families |= kFamGLRLM;
     if (f >= FR_GLSZM_BEGIN && f < FR_GLDM_BEGIN) j.families |= kFamGLSZM;
     if (f >= FR_GLDM_BEGIN && f < FR_NGTDM_BEGIN) j.families |= kFamGLDM;
-    if (f >= FR_NGTDM_BEGIN) j.families |= kFamNGTDM;
+    if (f >= FR_NGTDM_BEGIN && f < FR_EXTRAS_BEGIN) j.families |= kFamNGTDM;
+    if (f >= kGlcmExtra && f < kGldmExtra) j.families |= kFamGLCM;
+    if (f >= kGldmExtra && f < kNumFeatures) j.families |= kFamGLDM;
   }
-  for (int f = kNumFeatures; f < 96; ++f) j.row_of[f] = -1;
+  for (int f = kNumFeatures; f < kRowOf; ++f) j.row_of[f] = -1;
   j.nf = row;
   j.ngc = j.p.disc_mode == FR_FBN ? j.p.bin_count : 255;
 }
@@ -827,7 +835,7 @@ fr_status scalar_open(fr_scalar& S, const fr_map_params* p, const uint8_t* mask)
     S.d_run = dev_alloc<void*>(2, &S.bytes);
     S.d_queue = dev_alloc<uint32_t>(1, &S.bytes);
     S.d_status = dev_alloc<int32_t>(1, &S.bytes);
-    S.d_row_of = dev_alloc<int16_t>(96, &S.bytes);
+    S.d_row_of = dev_alloc<int16_t>(kRowOf, &S.bytes);
     FR_TRY(cudaMemcpyAsync(S.d_row_of, j.row_of, sizeof(j.row_of), cudaMemcpyHostToDevice, s));
     // count buffers (cleared per run) first, then the rest
     const int ngc = j.ngc;
@@ -853,8 +861,8 @@ fr_status scalar_open(fr_scalar& S, const fr_map_params* p, const uint8_t* mask)
     S.key_bytes = (size_t)hcap * 8;
     const size_t o_parent = take((size_t)nvox * 4),
                  o_mccs = take((size_t)kNumDirs * ngc * ngc * 4),
-                 o_mccv = take((size_t)kNumDirs * 4 * ngc * 4), o_dirf = take(kNumDirs * 40 * 8),
-                 o_out = take(96 * 8);
+                 o_mccv = take((size_t)kNumDirs * 4 * ngc * 4), o_dirf = take(kNumDirs * kScalarDirF * 8),
+                 o_out = take(kRowOf * 8);
     S.scratch = dev_alloc<char>(off, &S.bytes);
     FrScalarArgs& A = S.A;
     memset((void*)&A, 0, sizeof(A));
@@ -919,7 +927,7 @@ void fr_map_params_init(fr_map_params* p, int32_t nx, int32_t ny, int32_t nz) {
   p->kernel_radius = 1;
   p->glcm_distance = 1;
   p->feature_mask[0] = ~0ull;
-  p->feature_mask[1] = (1ull << (kNumFeatures - 64)) - 1ull;
+  p->feature_mask[1] = (1ull << (kNumBench - 64)) - 1ull;  // the 93-map benchmark set
   p->kurtosis_excess = 1;
   p->device = 0;
   p->mask_on_device = 0;

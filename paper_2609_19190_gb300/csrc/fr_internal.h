@@ -7,7 +7,15 @@
 
 namespace fr {
 
-constexpr int kNumFeatures = 93;
+// Feature ids: 0..92 the 93-map benchmark set, 93..100 the IBSI extras that
+// complete the 101-map default set (3 statistics, 2 GLCM, 3 NGLDM).
+constexpr int kNumFeatures = 101;
+constexpr int kNumBench = 93;
+constexpr int kFirstExtra = 93;  // median abs. deviation, CoV, QCoD
+constexpr int kGlcmExtra = 96;   // sum variance, dissimilarity
+constexpr int kGldmExtra = 98;   // GLNUN, dependence count percentage, energy
+constexpr int kRowOf = 104;      // row_of entries (>= kNumFeatures)
+constexpr int kScalarDirF = 42;  // per-direction values of the scalar path
 constexpr int kNumDirs = 13;
 constexpr int kMaxRadius = 7;
 // Present-level count and level-range limits of the per-warp shared-memory
@@ -62,7 +70,7 @@ struct alignas(128) FrJob {
   uint32_t families;
   double bin_width;
   double voxel_volume;
-  int16_t row_of[96];  // output row of each feature id, -1 if not selected
+  int16_t row_of[kRowOf];  // output row of each feature id, -1 if not selected
 };
 
 // One work-queue entry: up to `n` voxels of one brick of one job.
@@ -139,8 +147,8 @@ struct FrScalarArgs {
   int64_t hcap;                // power of two >= 2 n_voi
   float* mcc_s;                // [13][ngc][ngc] deflated S matrices
   float* mcc_v;                // [13][4][ngc] solver vectors
-  double* dirf;                // [13][40] per-direction GLCM (24) + GLRLM (16)
-  double* out;                 // [93] feature values (written by the final kernel)
+  double* dirf;                // [13][kScalarDirF]: GLCM (24), GLRLM (16), GLCM extras (2)
+  double* out;                 // [kRowOf] feature values (written by the final kernel)
   int32_t* status;             // run status word
 };
 
@@ -223,7 +231,7 @@ inline FrArena fr_make_arena(int32_t r_max) {
   a.off_st = o;
   o += 264 * 2;
   a.off_fv = o;
-  o += 96 * 4;
+  o += kRowOf * 4;
   a.off_acc = o;
   o += 64 * 4;
   a.off_tmp = o;

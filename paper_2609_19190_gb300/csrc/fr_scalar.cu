@@ -281,7 +281,8 @@ __device__ __forceinline__ double sc_bregman(double d) {
 }
 
 // GLCM features of direction blockIdx.x (or of the merged matrix), written to
-// dirf[blockIdx.x][0..23].  Counts C(i, j): n for i != j, 2n on the diagonal.
+// dirf[blockIdx.x][0..23] (and the IBSI sum variance and dissimilarity at
+// [40..41]).  Counts C(i, j): n for i != j, 2n on the diagonal.
 __global__ void __launch_bounds__(kScThreads) sc_glcm_feat_kernel(const __grid_constant__ FrScalarArgs a) {
   __shared__ unsigned long long s_marg[256];
   __shared__ unsigned long long s_sbin[512];
@@ -289,10 +290,11 @@ __global__ void __launch_bounds__(kScThreads) sc_glcm_feat_kernel(const __grid_c
   __shared__ double s_red[16 * 32];
   __shared__ int s_present;
   const int d = blockIdx.x, tid = threadIdx.x;
-  double* f = a.dirf + d * 40;
+  double* f = a.dirf + d * kScalarDirF;
   const double kNaN = __longlong_as_double(0x7ff8000000000000ll);
   if (sc_failed(a)) {
     if (tid < 24) f[tid] = kNaN;
+    if (tid < 2) f[40 + tid] = kNaN;
     return;
   }
   const bool merged = a.agg == 1;
@@ -320,6 +322,7 @@ __global__ void __launch_bounds__(kScThreads) sc_glcm_feat_kernel(const __grid_c
   for (int i = 0; i < ng; ++i) T += s_marg[i];
   if (T == 0) {
     if (tid < 24) f[tid] = kNaN;
+    if (tid < 2) f[40 + tid] = kNaN;
     return;
   }
   const double dT = (double)T;
@@ -414,6 +417,10 @@ __global__ void __launch_bounds__(kScThreads) sc_glcm_feat_kernel(const __grid_c
       sa += k * p;
       se += sc_ent(p);
     }
+    double sv = 0.0;
+    for (int k = 2; k <= 2 * ng; ++k) sv += (k - sa) * (k - sa) * ((double)s_sbin[k] / dT);
+    f[40] = sv;
+    f[41] = da;
     const double mi_bits = v[15] * 1.4426950408889634;
     f[0] = v[0];
     f[1] = mu;
@@ -448,7 +455,7 @@ __global__ void __launch_bounds__(kScThreads) sc_glrlm_feat_kernel(const __grid_
   __shared__ double s_red[13 * 32];
   __shared__ unsigned long long s_ured[3 * 32];
   const int d = blockIdx.x, tid = threadIdx.x;
-  double* f = a.dirf + d * 40 + 24;
+  double* f = a.dirf + d * kScalarDirF + 24;
   const double kNaN = __longlong_as_double(0x7ff8000000000000ll);
   if (sc_failed(a)) {
     if (tid < 16) f[tid] = kNaN;
@@ -533,10 +540,10 @@ __global__ void __launch_bounds__(kScThreads) sc_glrlm_feat_kernel(const __grid_
 }
 
 // First order (block 0), GLSZM (block 1), GLDM and NGTDM (block 2), written
-// to out[0..17], out[58..92].
+// to out[0..17], out[58..92] and their extras out[93..95], out[98..100].
 __global__ void __launch_bounds__(kMiscThreads) sc_misc_feat_kernel(const __grid_constant__ FrScalarArgs a) {
   __shared__ double s_red[12 * 32];
-  __shared__ unsigned long long s_ured[3 * 32];
+  __shared__ unsigned long long s_ured[4 * 32];
   __shared__ unsigned long long s_base[kMiscThreads];
   __shared__ int s_val[10];
   __shared__ int s_mm[2];
@@ -546,8 +553,10 @@ __global__ void __launch_bounds__(kMiscThreads) sc_misc_feat_kernel(const __grid
   double* out = a.out;
   if (sc_failed(a)) {
     if (blockIdx.x == 0 && tid < 18) out[tid] = kNaN;
+    if (blockIdx.x == 0 && tid < 3) out[kFirstExtra + tid] = kNaN;
     if (blockIdx.x == 1 && tid < 16) out[58 + tid] = kNaN;
     if (blockIdx.x == 2 && tid < 19) out[74 + tid] = kNaN;
+    if (blockIdx.x == 2 && tid < 3) out[kGldmExtra + tid] = kNaN;
     return;
   }
   const int ng = a.state->ng;
@@ -623,7 +632,8 @@ __global__ void __launch_bounds__(kMiscThreads) sc_misc_feat_kernel(const __grid
       return 100 * xk + (rem ? rem * (xk1 - xk) : 0);
     };
     const long long r10 = pct100(0), r90 = pct100(4);
-    double m[6] = {0, 0, 0, 0, 0, 0};  // m2 m3 m4 mad, robust count, robust sum
+    const double med = pct(2);
+    double m[7] = {0, 0, 0, 0, 0, 0, 0};  // m2 m3 m4 mad, robust count, robust sum, |x - median|
     for (int b = b0; b < b0 + kPer; ++b) {
       const unsigned c = a.hraw[b];
       if (!c) continue;
@@ -632,13 +642,14 @@ __global__ void __launch_bounds__(kMiscThreads) sc_misc_feat_kernel(const __grid
       m[1] += dc * dv * dv * dv;
       m[2] += dc * dv * dv * dv * dv;
       m[3] += dc * fabs(dv);
+      m[6] += dc * fabs(xv - med);
       const long long x100 = 100ll * (b - 32768);
       if (x100 >= r10 && x100 <= r90) {
         m[4] += dc;
         m[5] += dc * xv;
       }
     }
-    block_sum<6>(m, s_red);
+    block_sum<7>(m, s_red);
     const double rmean = m[5] / m[4];
     double rm[1] = {0.0};
     for (int b = b0; b < b0 + kPer; ++b) {
@@ -676,6 +687,12 @@ __global__ void __launch_bounds__(kMiscThreads) sc_misc_feat_kernel(const __grid
       out[15] = m2 == 0.0 ? kNaN : m4 / (m2 * m2) - (a.kurt_excess ? 3.0 : 0.0);
       out[16] = m2;
       out[17] = e[1];
+      // IBSI extras: median absolute deviation, coefficient of variation,
+      // quartile coefficient of dispersion
+      const double p25 = pct(1), p75 = pct(3);
+      out[kFirstExtra] = m[6] / N;
+      out[kFirstExtra + 1] = sc_div(sqrt(m2), mean);
+      out[kFirstExtra + 2] = sc_div(p75 - p25, p75 + p25);
     }
   } else if (blockIdx.x == 1) {
     // ---- GLSZM from zones per level, per size and per (level, size)
@@ -741,10 +758,15 @@ __global__ void __launch_bounds__(kMiscThreads) sc_misc_feat_kernel(const __grid
     }
   } else {
     // ---- GLDM from [level][equal neighbours] counts
-    unsigned long long u[3] = {0ull, 0ull, 0ull};  // N, sum rows^2, sum cols^2
+    // N, sum rows^2, sum cols^2, sum of squared cells
+    unsigned long long u[4] = {0ull, 0ull, 0ull, 0ull};
     for (int g = tid + 1; g <= ng; g += blockDim.x) {
       unsigned long long r = 0;
-      for (int j = 0; j < 27; ++j) r += a.gldm[g * 27 + j];
+      for (int j = 0; j < 27; ++j) {
+        const unsigned long long c = a.gldm[g * 27 + j];
+        r += c;
+        u[3] += c * c;
+      }
       u[0] += r;
       u[1] += r * r;
     }
@@ -753,7 +775,7 @@ __global__ void __launch_bounds__(kMiscThreads) sc_misc_feat_kernel(const __grid
       for (int g = 1; g <= ng; ++g) c += a.gldm[g * 27 + tid];
       u[2] += c * c;
     }
-    block_sum_u64<3>(u, s_ured);
+    block_sum_u64<4>(u, s_ured);
     const double N = (double)u[0];
     double m[2] = {0.0, 0.0};
     for (int t = tid; t < ng * 27; t += blockDim.x) {
@@ -835,6 +857,16 @@ __global__ void __launch_bounds__(kMiscThreads) sc_misc_feat_kernel(const __grid
         f[12] = v[9];
         f[13] = v[10];
       }
+      // IBSI extras: normalised gray level non-uniformity, dependence count
+      // percentage, dependence count energy
+      double* e = out + kGldmExtra;
+      if (u[0] == 0) {
+        for (int k = 0; k < 3; ++k) e[k] = kNaN;
+      } else {
+        e[0] = (double)u[1] / (N * N);
+        e[1] = N / (double)a.n_voi;
+        e[2] = (double)u[3] / (N * N);
+      }
       double* h = out + 88;
       if (Nvp == 0.0) {
         for (int k = 0; k < 5; ++k) h[k] = kNaN;
@@ -855,16 +887,16 @@ __global__ void sc_final_kernel(const __grid_constant__ FrScalarArgs a, double* 
   const double kNaN = __longlong_as_double(0x7ff8000000000000ll);
   const int ndir = a.agg == 1 ? 1 : kNumDirs;
   const bool bad = sc_failed(a);
-  for (int k = threadIdx.x; k < 40; k += blockDim.x) {
+  for (int k = threadIdx.x; k < kScalarDirF; k += blockDim.x) {
     double s = 0.0;
     int c = 0;
     for (int d = 0; d < ndir; ++d) {
-      const double v = a.dirf[d * 40 + k];
+      const double v = a.dirf[d * kScalarDirF + k];
       if (isnan(v)) continue;
       s += v;
       ++c;
     }
-    a.out[k < 24 ? 18 + k : 42 + (k - 24)] = c ? s / c : kNaN;
+    a.out[k < 24 ? 18 + k : k < 40 ? 42 + (k - 24) : kGlcmExtra + (k - 40)] = c ? s / c : kNaN;
   }
   __syncthreads();
   for (int f = threadIdx.x; f < kNumFeatures; f += blockDim.x) {

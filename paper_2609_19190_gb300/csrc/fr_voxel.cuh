@@ -298,7 +298,7 @@ static __device__ void first_order(Win& w, const Arena& A, const FrJob& job,
   }
   // pass 2: central moments from d = N x - S1 (exact), robust-range counts
   __int128 d2 = 0, d3 = 0, d4 = 0;
-  unsigned long long dabs = 0;
+  unsigned long long dabs = 0, medabs = 0;  // medabs: sum |100 x - 100 P50|
   unsigned below10 = 0, upto90 = 0;
   for (int i = lane; i < N; i += 32) {
     const long long x = xs(i);
@@ -308,6 +308,8 @@ static __device__ void first_order(Win& w, const Arena& A, const FrJob& job,
     d3 += (__int128)dd * d;
     d4 += (__int128)dd * dd;
     dabs += (unsigned long long)(d < 0 ? -d : d);
+    const long long dm = 100 * x - num[2];
+    medabs += (unsigned long long)(dm < 0 ? -dm : dm);
     below10 += (100 * x < num[0]);
     upto90 += (100 * x <= num[4]);
   }
@@ -315,6 +317,7 @@ static __device__ void first_order(Win& w, const Arena& A, const FrJob& job,
   d3 = warp_sum_i128(d3);
   d4 = warp_sum_i128(d4);
   dabs = warp_sum_u64(dabs);
+  medabs = warp_sum_u64(medabs);
   below10 = redux_u32(below10);
   upto90 = redux_u32(upto90);
   // pass 3: robust subset [below10, upto90)
@@ -361,6 +364,12 @@ static __device__ void first_order(Win& w, const Arena& A, const FrJob& job,
     }
     f[16] = __fdividef(m2, fn * fn * fn);
     f[17] = __fdividef((float)u2, fn * fn);
+    // IBSI extras: median absolute deviation, coefficient of variation
+    // sqrt(variance) / mean, quartile coefficient of dispersion (exact
+    // numerator and denominator 100 (P75 -+ P25))
+    f[kFirstExtra] = __fdividef((float)medabs, 100.f * fn);
+    f[kFirstExtra + 1] = lane_quot(sqrtf(__fdividef(m2, fn)), (float)s1);
+    f[kFirstExtra + 2] = lane_quot((float)(num[3] - num[1]), (float)(num[3] + num[1]));
   }
   w.m = m;
   w.lev0 = A.lev[0];
@@ -845,6 +854,9 @@ static __device__ void glcm_finish(const Arena& A, const FrJob& job) {
     }
   }
   acc_store(A, want_mcc ? 24 : 23, 18);
+  if (lane == 24 || lane == 25)
+    A.fv[kGlcmExtra + lane - 24] =
+        A.nacc[lane] ? __fdividef(A.facc[lane] + A.fcomp[lane], (float)A.nacc[lane]) : kNaNf;
   {
     __syncwarp();
     const int t = lane < kNumDirs ? cst[lane] : 0;
@@ -1209,7 +1221,7 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
     }
     // difference and sum distributions (bins relative to the smallest level)
     unsigned dk = 0, sk = 0;
-    unsigned long long dk2 = 0;
+    unsigned long long dk2 = 0, sk2 = 0;
     float de = 0.f, idm = 0.f, idmn = 0.f, idd = 0.f, idn = 0.f, iv = 0.f, se = 0.f,
           ce2 = 0.f, ce4 = 0.f;
     __int128 ce3 = 0;
@@ -1235,6 +1247,7 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
         sbin[k] = 0;
         const int kk = k + 2 * w.lev0;
         sk += (unsigned)(kk * c);
+        sk2 += (unsigned long long)(kk * kk) * (unsigned)c;
         se += ent_term(c, T);
         // T (k - 2 mu): |e| < 2^24 per direction, < 2^26 merged
         const int e = T * kk - 2 * (int)m1;
@@ -1246,6 +1259,7 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
     }
     dk = redux_u32(dk);
     dk2 = merged ? warp_sum_u64(dk2) : redux_u32((unsigned)dk2);
+    sk2 = merged ? warp_sum_u64(sk2) : redux_u32((unsigned)sk2);
     sk = redux_u32(sk);
     ce3 = warp_sum_i128(ce3);
     float fs[12] = {hx, hxy, mi, de, idm, idmn, idd, idn, iv, se, ce2, ce4};
@@ -1282,7 +1296,10 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
     if (lane == 20) { num = (float)sk; den = fT; }
     if (lane == 21) { num = fs[9]; }
     if (lane == 22) { num = (float)var_num; den = fT * fT; }
-    acc_lane(A, 23, lane_quot(num, den));
+    // IBSI extras (lanes 24, 25): sum variance, dissimilarity
+    if (lane == 24) { num = (float)((long long)T * (long long)sk2 - (long long)sk * sk); den = fT * fT; }
+    if (lane == 25) { num = (float)dk; den = fT; }
+    acc_lane(A, 26, lane_quot(num, den));
   }
 }
 
@@ -1930,7 +1947,7 @@ static __device__ void gldm_ngtdm_family(const Win& w, const Arena& A, const FrJ
   __syncwarp();
   const int N = w.nv;
   if (do_gldm) {
-    unsigned si = 0, si2 = 0, sj = 0, sj2 = 0, dnu = 0;
+    unsigned si = 0, si2 = 0, sj = 0, sj2 = 0, dnu = 0, dce = 0;  // dce: sum c^2
     float fs[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sde lgl sdl sdh ldl ldh de
     for (int a0 = 0; a0 < m; a0 += 32) {
       const int a = a0 + lane;
@@ -1959,6 +1976,7 @@ static __device__ void gldm_ngtdm_family(const Win& w, const Arena& A, const FrJ
           fs[4] += fc * fj2 * inv_i2;
           fs[5] += fc * fi2 * fj2;
           fs[6] += ent_term(c, N);
+          dce += (unsigned)(c * c);
           if (dbg_gldm) dbg_gldm[(i - 1) * 27 + k] = c;
         }
       }
@@ -1976,6 +1994,7 @@ static __device__ void gldm_ngtdm_family(const Win& w, const Arena& A, const FrJ
     si2 = redux_u32(si2);
     sj = redux_u32(sj);
     sj2 = redux_u32(sj2);
+    dce = redux_u32(dce);
     warp_sum_f32x<7>(fs);
     const float fN = (float)N;
     float num = kNaNf, den = fN;
@@ -1993,7 +2012,13 @@ static __device__ void gldm_ngtdm_family(const Win& w, const Arena& A, const FrJ
     if (lane == 11) { num = fs[3]; }
     if (lane == 12) { num = fs[4]; }
     if (lane == 13) { num = fs[5]; }
+    // IBSI extras: grey level non-uniformity normalised, dependence count
+    // percentage N / N_v, dependence count energy sum p^2
+    if (lane == 14) { num = (float)w.u2; den = fN * fN; }
+    if (lane == 15) { num = fN; den = (float)w.nv; }
+    if (lane == 16) { num = (float)dce; den = fN * fN; }
     if (lane < 14) A.fv[74 + lane] = lane_quot(num, den);
+    if (lane >= 14 && lane < 17) A.fv[kGldmExtra + lane - 14] = lane_quot(num, den);
   }
   __syncwarp();
   if (do_ngtdm) {

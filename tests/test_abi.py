@@ -67,7 +67,7 @@ def test_params_init_defaults():
     p = fm.fr_map_params_init(10, 11, 12)
     assert (p.nx, p.ny, p.nz) == (10, 11, 12)
     assert p.disc_mode == fm.FR_FBN and p.bin_count == 16 and p.kernel_radius == 1
-    assert fm.selected_features(p) == list(range(93))
+    assert fm.selected_features(p) == list(range(93))  # the benchmark maps by default
     q = fm.fr_map_params_init(4, 4, 4, features=[18, 19, 41], kernel_radius=3)
     assert fm.selected_features(q) == [18, 19, 41] and q.kernel_radius == 3
 
@@ -92,5 +92,6 @@ def test_invalid_arguments_are_rejected_without_a_device():
     assert L.fr_map_sync_status(None) == 1
     L.fr_map_destroy(None)
     L.fr_batch_destroy(None)
-    assert L.fr_feature_name(93) is None and L.fr_feature_count() == 93
+    assert L.fr_feature_name(101) is None and L.fr_feature_count() == 101
+    assert L.fr_feature_name(93) == b"firstorder_MedianAbsoluteDeviation"
     assert L.fr_status_string(3) == b"more than 255 gray levels"

@@ -11,6 +11,8 @@ from paper_2609_19190_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
+ALL = list(range(101))  # the 93 benchmark maps and the 8 IBSI extras (Table 2)
+
 
 def _fm():
     import paper_2609_19190_gb300 as fm
@@ -122,7 +124,8 @@ def test_single_voxel_voi_and_isolated_voxels():
     m1[10, 15, 16] = 1
     m1[2, 2, 2] = 1
     m1[2, 2, 4] = 1  # two voxels two apart: each window holds one or two
-    got, plan, feats = H.gpu_map(img, m1, disc_mode=0, bin_count=8, kernel_radius=1)
+    got, plan, feats = H.gpu_map(img, m1, features=ALL, disc_mode=0, bin_count=8,
+                                 kernel_radius=1)
     ref, _, _, _ = H.oracle_map(img, m1, disc_mode=0, bin_count=8, kernel_radius=1)
     parity.assert_close(got, ref[feats], [O.feature_names()[f] for f in feats])
 
@@ -132,7 +135,7 @@ def test_voi_on_the_borders_odd_extent_radius3():
     img = rng.integers(-200, 200, size=(9, 11, 13)).astype(np.int16)
     mask = (rng.random(img.shape) < 0.8).astype(np.uint8)
     kw = dict(disc_mode=0, bin_count=12, kernel_radius=3)
-    got, plan, feats = H.gpu_map(img, mask, **kw)
+    got, plan, feats = H.gpu_map(img, mask, features=ALL, **kw)
     ref, _, _, _ = H.oracle_map(img, mask, **kw)
     parity.assert_close(got, ref[feats], [O.feature_names()[f] for f in feats])
 
@@ -143,7 +146,7 @@ def test_max_radius_seven():
     mask = (rng.random(img.shape) < 0.6).astype(np.uint8)
     kw = dict(disc_mode=0, bin_count=6, kernel_radius=7)
     vox = synth.sample_voxels(mask, 150, seed=1)
-    got, plan, feats = H.gpu_map(img, mask, **kw)
+    got, plan, feats = H.gpu_map(img, mask, features=ALL, **kw)
     cols = np.searchsorted(np.flatnonzero(mask.reshape(-1)), vox)
     ref, _, _, _ = H.oracle_map(img, mask, voxels=vox, **kw)
     parity.assert_close(got[:, cols], ref[feats], [O.feature_names()[f] for f in feats])
@@ -152,7 +155,7 @@ def test_max_radius_seven():
 def test_glcm_distance_two_and_zero_floor_anchor():
     img, mask = _ct(seed=13)
     kw = dict(disc_mode=1, bin_width=20.0, fbw_anchor=1, kernel_radius=2, glcm_distance=2)
-    got, plan, feats = H.gpu_map(img, mask, **kw)
+    got, plan, feats = H.gpu_map(img, mask, features=ALL, **kw)
     ref, _, _, _ = H.oracle_map(img, mask, **kw)
     parity.assert_close(got, ref[feats], [O.feature_names()[f] for f in feats])
 
@@ -162,7 +165,8 @@ def test_constant_and_two_level_images():
     mask = np.zeros_like(img, dtype=np.uint8)
     mask[1:9, 1:9, 1:9] = 1
     for im in (img, np.where((np.indices(img.shape).sum(0) % 2) == 0, 10, 90).astype(np.int16)):
-        got, plan, feats = H.gpu_map(im, mask, disc_mode=0, bin_count=4, kernel_radius=2)
+        got, plan, feats = H.gpu_map(im, mask, features=ALL, disc_mode=0, bin_count=4,
+                                     kernel_radius=2)
         ref, _, _, _ = H.oracle_map(im, mask, disc_mode=0, bin_count=4, kernel_radius=2)
         parity.assert_close(got, ref[feats], [O.feature_names()[f] for f in feats])
 
@@ -174,7 +178,7 @@ def test_many_levels_use_the_slab_and_match():
     mask = np.ones(img.shape, np.uint8)
     kw = dict(disc_mode=0, bin_count=255, kernel_radius=2)
     vox = synth.sample_voxels(mask, 200, seed=2)
-    got, plan, feats = H.gpu_map(img, mask, **kw)
+    got, plan, feats = H.gpu_map(img, mask, features=ALL, **kw)
     ref, _, _, _ = H.oracle_map(img, mask, voxels=vox, **kw)
     cols = np.searchsorted(np.flatnonzero(mask.reshape(-1)), vox)
     parity.assert_close(got[:, cols], ref[feats], [O.feature_names()[f] for f in feats])

@@ -66,7 +66,7 @@ def test_batched_workload_items_against_oracle_sampled():
         img, mask, r, bins = synth.batch_item(i)
         kw = dict(disc_mode=0, bin_count=bins, kernel_radius=r)
         nz, ny, nx = img.shape
-        params.append(fm.fr_map_params_init(nx, ny, nz, **kw))
+        params.append(fm.fr_map_params_init(nx, ny, nz, features=list(range(101)), **kw))
         masks.append(torch.from_numpy(mask))
         imgs.append(torch.from_numpy(img).cuda())
         host.append((img, mask))

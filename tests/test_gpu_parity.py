@@ -15,6 +15,7 @@ from paper_2609_19190_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 NAMES = None
+ALL = list(range(101))  # the 93 benchmark maps and the 8 IBSI extras (Table 2)
 
 
 def names():
@@ -56,25 +57,31 @@ def test_tiny_fbn24_r2_many_levels_per_window():
     # of what the shared-memory arena takes (every family's matrices over
     # high compact levels; MCC on more than 12 levels)
     img, mask = synth.tiny(seed=1)
-    _check(img, mask, disc_mode=0, bin_count=24, kernel_radius=2)
+    _check(img, mask, features=ALL, disc_mode=0, bin_count=24, kernel_radius=2)
 
 
-def test_tiny_all_93_full():
+def test_tiny_all_101_full():
     img, mask = synth.tiny(seed=1)
-    _check(img, mask, disc_mode=0, bin_count=16, kernel_radius=1)
+    _check(img, mask, features=ALL, disc_mode=0, bin_count=16, kernel_radius=1)
+
+
+def test_tiny_default_is_the_93_benchmark_maps():
+    img, mask = synth.tiny(seed=1)
+    plan = _check(img, mask, disc_mode=0, bin_count=16, kernel_radius=1)
+    assert plan.features == list(range(93))
 
 
 @pytest.mark.parametrize("r", [1, 2, 3])
-def test_ct_crop_all_93_fbw(r):
+def test_ct_crop_all_101_fbw(r):
     img, mask = _crop_ct()
-    _check(img, mask, disc_mode=1, bin_width=25.0, kernel_radius=r)
+    _check(img, mask, features=ALL, disc_mode=1, bin_width=25.0, kernel_radius=r)
 
 
 @pytest.mark.parametrize("r", [1, 2, 3])
-def test_ct_crop_all_93_merged_aggregation(r):
+def test_ct_crop_all_101_merged_aggregation(r):
     # GLCM and GLRLM over the sum of the 13 directional matrices
     img, mask = _crop_ct(seed=6, shape=(16, 28, 32), semi=(14.0, 12.0, 7.0))
-    _check(img, mask, disc_mode=1, bin_width=25.0, kernel_radius=r, aggregation=1)
+    _check(img, mask, features=ALL, disc_mode=1, bin_width=25.0, kernel_radius=r, aggregation=1)
 
 
 def test_tiny_merged_aggregation_fbn16():
@@ -86,7 +93,7 @@ def test_ct_crop_fbn64_r3_slab_path():
     # FBN 64 makes windows with more than 32 levels or a level range >= 64
     # possible; the kernel then uses its global slab.
     img, mask = _crop_ct(seed=5)
-    _check(img, mask, disc_mode=0, bin_count=64, kernel_radius=3)
+    _check(img, mask, features=ALL, disc_mode=0, bin_count=64, kernel_radius=3)
 
 
 def test_levels_and_voxel_list_bit_exact():

@@ -16,6 +16,7 @@ from paper_2609_19190_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 MCC = 41
+ALL = list(range(101))  # the 93 benchmark features and the 8 IBSI extras (Table 2)
 
 
 def _gpu_scalar(img, mask, **kw):
@@ -71,24 +72,25 @@ def _crop_ct(seed, shape, semi):
 
 def test_scalar_tiny_fbn16():
     img, mask = synth.tiny(seed=1)
-    _check(img, mask, disc_mode=0, bin_count=16)
+    _check(img, mask, disc_mode=0, bin_count=16, features=ALL)
 
 
 @pytest.mark.parametrize("agg", [0, 1])
 def test_scalar_ct_crop_fbw(agg):
     img, mask = _crop_ct(3, (24, 40, 44), (19.0, 16.0, 10.0))
-    _check(img, mask, disc_mode=1, bin_width=25.0, aggregation=agg, spacing=(0.8, 0.8, 2.0))
+    _check(img, mask, disc_mode=1, bin_width=25.0, aggregation=agg, spacing=(0.8, 0.8, 2.0),
+           features=ALL)
 
 
 def test_scalar_ct_plain_full_size_fbw25():
-    # the 128 x 128 x 64 CT-like volume, VOI of 200,336 voxels, all 93 features
+    # the 128 x 128 x 64 CT-like volume, VOI of 200,336 voxels, all 101 features
     img, mask = synth.ct_plain(seed=2)
-    _check(img, mask, disc_mode=1, bin_width=25.0)
+    _check(img, mask, disc_mode=1, bin_width=25.0, features=ALL)
 
 
 def test_scalar_fbn64_delta2_subset():
     img, mask = _crop_ct(4, (20, 36, 30), (14.0, 16.0, 9.0))
-    feats = [0, 4, 8, 18, 24, 30, 31, 41, 42, 48, 58, 64, 74, 88, 90]
+    feats = [0, 4, 8, 18, 24, 30, 31, 41, 42, 48, 58, 64, 74, 88, 90, 93, 95, 96, 97, 99]
     _check(img, mask, disc_mode=0, bin_count=64, glcm_distance=2, features=feats)
 
 
@@ -99,8 +101,8 @@ def test_scalar_equals_map_where_windows_cover_the_voi():
     mask = np.zeros(img.shape, np.uint8)
     mask[5:12, 4:11, 6:13] = rng.random((7, 7, 7)) < 0.75
     kw = dict(disc_mode=0, bin_count=12)
-    sc, _ = _gpu_scalar(img, mask, **dict(kw))
-    maps, plan, feats = H.gpu_map(img, mask, kernel_radius=7, **kw)
+    sc, _ = _gpu_scalar(img, mask, features=ALL, **dict(kw))
+    maps, plan, feats = H.gpu_map(img, mask, features=ALL, kernel_radius=7, **kw)
     for f in feats:
         if f == MCC:
             continue
@@ -115,13 +117,13 @@ def test_scalar_runs_are_deterministic_outside_glszm():
 
     import paper_2609_19190_gb300 as fm
     nz, ny, nx = img.shape
-    p = fm.fr_map_params_init(nx, ny, nz, disc_mode=1, bin_width=25.0)
+    p = fm.fr_map_params_init(nx, ny, nz, disc_mode=1, bin_width=25.0, features=ALL)
     sp = fm.fr_scalar_plan(p, torch.from_numpy(mask))
     dimg = torch.from_numpy(img).cuda()
     a = fm.fr_scalar_run(sp, dimg).cpu().numpy()
     b = fm.fr_scalar_run(sp, dimg).cpu().numpy()
     fm.fr_scalar_sync_status(sp)
-    keep = [k for k in range(93) if not 58 <= k < 74]
+    keep = [k for k in ALL if not 58 <= k < 74]
     assert np.array_equal(a[keep].view(np.int64), b[keep].view(np.int64))
     np.testing.assert_allclose(a[58:74], b[58:74], rtol=1e-12)
 
