@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-scalar", action="store_true")
+    ap.add_argument("--no-drain", action="store_true")
     ap.add_argument("--batch-vois", type=int, default=64)
     ap.add_argument("--served-requests", type=int, default=120)
     ap.add_argument("--served-rates", default="10,50,100,200")
@@ -420,6 +421,36 @@ def measure_scalar(img, mask, kw, dev, steps):
                     "features from exact counts"}
 
 
+def measure_drain(plan, params, out, img, mask):
+    """Host-side HDF5 drain of the finished maps (fr_h5_write_maps): dense
+    [nz][ny][nx] float32 maps with NaN outside the VOI, image, mask, geometry
+    and settings, chunks encoded on all host threads; wall time per file."""
+    import shutil
+    import tempfile
+
+    import paper_2609_19190_gb300 as fm
+    maps = out.cpu().numpy()
+    vox = fm.fr_plan_voxel_index(plan).cpu().numpy()
+    tmp = tempfile.mkdtemp(prefix="fr_drain_")
+    res = {"threads": os.cpu_count(), "raw_dense_mb": maps.shape[0] * img.size * 4 / 1e6}
+    try:
+        for codec in ("gzip", "lzf"):
+            path = os.path.join(tmp, "maps_%s.h5" % codec)
+            ts = []
+            for _ in range(2):
+                t0 = time.perf_counter()
+                fm.fr_h5_write_maps(path, params, img, mask, maps, vox, codec=codec, level=1,
+                                    source_id="bench volume")
+                ts.append(time.perf_counter() - t0)
+            res[codec] = {"seconds": min(ts), "file_mb": os.path.getsize(path) / 1e6,
+                          "dense_mb_per_s": res["raw_dense_mb"] / min(ts)}
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+    res["note"] = ("one HDF5 file per extraction: %d dense maps + image + mask, byte shuffle "
+                   "then gzip level 1 or LZF; host wall time, best of 2" % maps.shape[0])
+    return res
+
+
 def run_flashmap(args):
     import torch
     import paper_2609_19190_gb300 as fm
@@ -513,6 +544,9 @@ def run_flashmap(args):
     scalar = None
     if not args.no_scalar:
         scalar = measure_scalar(img, mask, kw, dev, args.steps)
+    drain = None
+    if not args.no_drain and world == 1:
+        drain = measure_drain(plan, params, out, img, mask)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         rate, cores, n, dt, _ = oracle_rate(img, mask, kw, args.cpu_seconds)
@@ -530,7 +564,7 @@ def run_flashmap(args):
                                             "feeds the TMA halo copies",
                               "tune": tune}},
         "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
-        "batched": batched, "served": served, "scalar": scalar,
+        "batched": batched, "served": served, "scalar": scalar, "drain": drain,
         "gpu_launches": 4 * args.steps,
     }
     print(json.dumps(line), flush=True)

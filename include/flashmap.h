@@ -60,7 +60,8 @@ typedef enum fr_status {
   FR_ERR_CUDA = 5,            /* a CUDA runtime or driver call failed */
   FR_ERR_TIMEOUT = 6,         /* a bounded device wait ran out */
   FR_ERR_UNSUPPORTED = 7,     /* no usable sm_103a device, or a size beyond a limit */
-  FR_ERR_MISMATCH = 8         /* arguments disagree with the plan (debug calls) */
+  FR_ERR_MISMATCH = 8,        /* arguments disagree with the plan (debug calls) */
+  FR_ERR_IO = 9               /* a file could not be created or written (HDF5 drain) */
 } fr_status;
 
 enum { FR_FBN = 0, FR_FBW = 1 };                             /* discretisation */
@@ -297,9 +298,67 @@ fr_status fr_voxel_list_noalloc(const uint8_t* mask, int32_t nx, int32_t ny, int
                                 int32_t* voi, int64_t capacity, int64_t* n_voi,
                                 int32_t device, fr_stream_t s);
 
+/* ---- HDF5 drain of finished results (host only; the paper's "Structured
+ * HDF5 storage": one file per extraction with the results, the image and
+ * mask arrays, the voxel geometry, the extraction settings and the input's
+ * identification; scalar results as ordered feature names and float64
+ * values, spatial results as named maps; LZF or gzip compression).
+ *
+ * File layout (HDF5, superblock version 0, readable by any HDF5 reader):
+ *   /image     int16 [nz][ny][nx]   chunked, compressed
+ *   /mask      uint8 [nz][ny][nx]   chunked, compressed
+ *   /maps/<feature name>   float32 [nz][ny][nx], NaN outside the VOI, one
+ *              per selected feature (spatial files); attribute feature_id.
+ *              Chunks holding no VOI voxel are not stored (fill value NaN).
+ *   /features/names  fixed-length strings [n], /features/values float64 [n]
+ *              in feature-id order (scalar files)
+ *   root attributes: format, mode ("spatial" / "scalar"), shape_zyx,
+ *   spacing_xyz_mm, origin_xyz_mm, discretisation, bin_count, bin_width,
+ *   fbw_anchor, kernel_radius, glcm_distance, aggregation, kurtosis_excess,
+ *   feature_ids, source, created_utc, writer.
+ * Chunks are encoded on host threads; gzip needs the system zlib (libz.so.1,
+ * loaded at first use; without it gzip returns FR_ERR_UNSUPPORTED).  The
+ * chunk grid holds at most 64 chunks (requested extents grow until it does).
+ * Errors: INVALID_ARG (NULL pointer, bad option, row count not matching the
+ * selection, voxel index outside the volume), UNSUPPORTED, OOM, IO (the file
+ * could not be created or written; a partial file may remain). */
+enum { FR_H5_NONE = 0, FR_H5_GZIP = 1, FR_H5_LZF = 2 };
+
+typedef struct fr_h5_options {
+  int32_t codec;    /* FR_H5_NONE, FR_H5_GZIP (default) or FR_H5_LZF            */
+  int32_t level;    /* gzip level 1..9 (0: 4)                                   */
+  int32_t shuffle;  /* 1: HDF5 byte-shuffle filter before the codec (default)   */
+  int32_t threads;  /* host threads encoding chunks (0: all hardware threads)   */
+  int32_t chunk[3]; /* chunk extents z, y, x (0: a quarter of the extent)       */
+} fr_h5_options;
+
+/* The extraction's input, all host memory owned by the caller. */
+typedef struct fr_h5_source {
+  const int16_t* image;  /* [nz][ny][nx]                                        */
+  const uint8_t* mask;   /* [nz][ny][nx], nonzero = VOI                         */
+  double origin[3];      /* position of voxel (0,0,0) in mm, x y z              */
+  const char* source_id; /* identifies the input (path, UID ...); may be NULL   */
+} fr_h5_source;
+
+/* Defaults: gzip level 4 with shuffle, all threads, automatic chunks. */
+fr_status fr_h5_options_init(fr_h5_options* o);
+
+/* Spatial extraction: maps (host float32 [n_rows][n_voi], the fr_map_run
+ * output for p's selection) with voxel_index (host int32 [n_voi], the
+ * linear index z-major of each column, as fr_plan_voxel_index gives).
+ * n_rows must equal the number of features p selects.  opt may be NULL. */
+fr_status fr_h5_write_maps(const char* path, const fr_map_params* p, const fr_h5_source* src,
+                           const float* maps, int32_t n_rows, int64_t n_voi,
+                           const int32_t* voxel_index, const fr_h5_options* opt);
+
+/* Scalar extraction: values (host float64 [n_values], the fr_scalar_run
+ * output for p's selection, feature-id order).  opt may be NULL. */
+fr_status fr_h5_write_scalar(const char* path, const fr_map_params* p, const fr_h5_source* src,
+                             const double* values, int32_t n_values, const fr_h5_options* opt);
+
 /* Names and helpers. */
 int32_t fr_feature_count(void);
-const char* fr_feature_name(int32_t id); /* NULL outside 0..92 */
+const char* fr_feature_name(int32_t id); /* NULL outside 0..100 */
 const char* fr_status_string(fr_status s);
 /* Direction i (0..12) as (dz, dy, dx); INVALID_ARG outside 0..12. */
 fr_status fr_direction(int32_t i, int32_t* dz, int32_t* dy, int32_t* dx);

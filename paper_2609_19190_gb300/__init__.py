@@ -18,8 +18,8 @@ import ctypes as C
 
 from . import _lib
 from ._lib import (FR_ANCHOR_VOI_MIN, FR_ANCHOR_ZERO_FLOOR, FR_FBN, FR_FBW,  # noqa: F401
-                   FR_NUM_DIRECTIONS, FR_NUM_FEATURES, FlashmapError, MapParams, Tune,
-                   check)
+                   FR_H5_GZIP, FR_H5_LZF, FR_H5_NONE, FR_NUM_DIRECTIONS, FR_NUM_FEATURES,
+                   FlashmapError, MapParams, Tune, check)
 
 __all__ = [
     "fr_map_params_init", "fr_map_plan", "fr_map_run", "fr_map_run_host",
@@ -28,7 +28,7 @@ __all__ = [
     "fr_plan_last_kernel_ms", "fr_batch_last_kernel_ms",
     "fr_batch_run", "fr_batch_sync_status", "fr_batch_query", "fr_batch_destroy",
     "fr_feature_names", "fr_direction", "FR_FBN", "FR_FBW", "MapParams", "Tune",
-    "FlashmapError",
+    "FlashmapError", "fr_h5_write_maps", "fr_h5_write_scalar",
 ]
 
 FAMILIES = {
@@ -393,3 +393,62 @@ def fr_direction(i):
     a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
     check("fr_direction", _lib.load().fr_direction(i, C.byref(a), C.byref(b), C.byref(c)))
     return a.value, b.value, c.value
+
+
+_CODECS = {"none": FR_H5_NONE, "gzip": FR_H5_GZIP, "lzf": FR_H5_LZF}
+
+
+def _h5_args(image, mask, origin, source_id, codec, level, shuffle, threads, chunk):
+    import numpy as np
+    img = np.ascontiguousarray(_host(image), dtype=np.int16)
+    msk = np.ascontiguousarray(_host(mask), dtype=np.uint8)
+    src = _lib.H5Source()
+    src.image = img.ctypes.data
+    src.mask = msk.ctypes.data
+    src.origin[:] = [float(v) for v in origin]
+    src.source_id = None if source_id is None else str(source_id).encode()
+    opt = _lib.H5Options()
+    check("fr_h5_options_init", _lib.load().fr_h5_options_init(C.byref(opt)))
+    opt.codec = _CODECS[codec]
+    opt.level = int(level)
+    opt.shuffle = 1 if shuffle else 0
+    opt.threads = int(threads)
+    opt.chunk[:] = list(chunk) if chunk is not None else [0, 0, 0]
+    return img, msk, src, opt
+
+
+def _host(x):
+    import numpy as np
+    if hasattr(x, "detach"):
+        return x.detach().cpu().numpy()
+    return np.asarray(x)
+
+
+def fr_h5_write_maps(path, params, image, mask, maps, voxel_index, origin=(0.0, 0.0, 0.0),
+                     source_id=None, codec="gzip", level=4, shuffle=True, threads=0,
+                     chunk=None):
+    """Write one spatial extraction to an HDF5 file (host side).  image / mask:
+    [nz][ny][nx] int16 / uint8; maps: float32 [rows][n_voi] (fr_map_run's
+    output, cpu or cuda); voxel_index: int32 [n_voi] (fr_plan_voxel_index)."""
+    import numpy as np
+    img, msk, src, opt = _h5_args(image, mask, origin, source_id, codec, level, shuffle, threads,
+                                  chunk)
+    m = np.ascontiguousarray(_host(maps), dtype=np.float32)
+    vi = np.ascontiguousarray(_host(voxel_index), dtype=np.int32)
+    check("fr_h5_write_maps", _lib.load().fr_h5_write_maps(
+        str(path).encode(), C.byref(params), C.byref(src), C.c_void_p(m.ctypes.data),
+        m.shape[0], m.shape[1], C.c_void_p(vi.ctypes.data), C.byref(opt)))
+
+
+def fr_h5_write_scalar(path, params, image, mask, values, origin=(0.0, 0.0, 0.0),
+                       source_id=None, codec="gzip", level=4, shuffle=True, threads=0,
+                       chunk=None):
+    """Write one scalar extraction (float64 values in feature-id order, as
+    fr_scalar_run gives) to an HDF5 file (host side)."""
+    import numpy as np
+    img, msk, src, opt = _h5_args(image, mask, origin, source_id, codec, level, shuffle, threads,
+                                  chunk)
+    v = np.ascontiguousarray(_host(values), dtype=np.float64)
+    check("fr_h5_write_scalar", _lib.load().fr_h5_write_scalar(
+        str(path).encode(), C.byref(params), C.byref(src), C.c_void_p(v.ctypes.data), v.size,
+        C.byref(opt)))

@@ -12,7 +12,7 @@ FR_OK = 0
 STATUS_NAMES = {
     0: "FR_OK", 1: "FR_ERR_INVALID_ARG", 2: "FR_ERR_EMPTY_MASK",
     3: "FR_ERR_TOO_MANY_LEVELS", 4: "FR_ERR_OOM", 5: "FR_ERR_CUDA",
-    6: "FR_ERR_TIMEOUT", 7: "FR_ERR_UNSUPPORTED", 8: "FR_ERR_MISMATCH",
+    6: "FR_ERR_TIMEOUT", 7: "FR_ERR_UNSUPPORTED", 8: "FR_ERR_MISMATCH", 9: "FR_ERR_IO",
 }
 
 FR_FBN, FR_FBW = 0, 1
@@ -20,6 +20,7 @@ FR_ANCHOR_VOI_MIN, FR_ANCHOR_ZERO_FLOOR = 0, 1
 FR_NUM_FEATURES = 101
 FR_NUM_BENCH_FEATURES = 93  # ids 0..92: the benchmark maps (the default selection)
 FR_NUM_DIRECTIONS = 13
+FR_H5_NONE, FR_H5_GZIP, FR_H5_LZF = 0, 1, 2
 
 
 class MapParams(C.Structure):
@@ -40,6 +41,20 @@ class Tune(C.Structure):
         ("brick_x", C.c_int32), ("brick_y", C.c_int32), ("brick_z", C.c_int32),
         ("voxels_per_item", C.c_int32), ("consumer_warps", C.c_int32),
         ("stages", C.c_int32), ("ctas_per_sm", C.c_int32),
+    ]
+
+
+class H5Options(C.Structure):
+    _fields_ = [
+        ("codec", C.c_int32), ("level", C.c_int32), ("shuffle", C.c_int32),
+        ("threads", C.c_int32), ("chunk", C.c_int32 * 3),
+    ]
+
+
+class H5Source(C.Structure):
+    _fields_ = [
+        ("image", C.c_void_p), ("mask", C.c_void_p), ("origin", C.c_double * 3),
+        ("source_id", C.c_char_p),
     ]
 
 
@@ -85,6 +100,11 @@ SIGNATURES = {
     "fr_server_query": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_size_t)]),
     "fr_server_destroy": (None, [_P]),
+    "fr_h5_options_init": (C.c_int, [C.POINTER(H5Options)]),
+    "fr_h5_write_maps": (C.c_int, [C.c_char_p, C.POINTER(MapParams), C.POINTER(H5Source), _P,
+                                   C.c_int32, C.c_int64, _P, C.POINTER(H5Options)]),
+    "fr_h5_write_scalar": (C.c_int, [C.c_char_p, C.POINTER(MapParams), C.POINTER(H5Source), _P,
+                                     C.c_int32, C.POINTER(H5Options)]),
     "fr_feature_count": (C.c_int32, []),
     "fr_feature_name": (C.c_char_p, [C.c_int32]),
     "fr_status_string": (C.c_char_p, [C.c_int]),

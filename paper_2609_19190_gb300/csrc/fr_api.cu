@@ -1530,6 +1530,7 @@ const char* fr_status_string(fr_status s) {
     case FR_ERR_TIMEOUT: return "device wait timed out";
     case FR_ERR_UNSUPPORTED: return "unsupported device or size";
     case FR_ERR_MISMATCH: return "arguments disagree with the plan";
+    case FR_ERR_IO: return "file could not be written";
   }
   return "unknown status";
 }

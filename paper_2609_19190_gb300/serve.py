@@ -90,7 +90,7 @@ def request_bytes(shape, n_voi, n_rows, brick=(8, 4, 4), voxels_per_item=16):
 
 def serve(requests, images, rate, *, seed=0, voxel_budget=65536, hbm_reserve=4 << 30,
           hbm_budget=None, device=0, max_radius=3, keep_outputs=False, tune=None,
-          time_limit=None):
+          time_limit=None, drain_dir=None, drain_codec="gzip", drain_workers=2):
     """Run the request stream; returns a dict of statistics (and the outputs
     by request index when keep_outputs).
 
@@ -98,7 +98,11 @@ def serve(requests, images, rate, *, seed=0, voxel_budget=65536, hbm_reserve=4 <
     overrides), n_voi, and either image_key (a key of `images`, device int16
     tensors) or the shape used as the key.  rate: mean arrivals per second.
     hbm_budget: admit against this many bytes instead of the driver's free
-    memory (the in-use figure is the sum of admitted estimates)."""
+    memory (the in-use figure is the sum of admitted estimates).
+    drain_dir: write each finished request to <drain_dir>/request_<i>.h5
+    (fr_h5_write_maps) on host worker threads, off the GPU loop; the maps are
+    copied to the host first, so the request's device memory is released at
+    once.  Latencies count up to the device result, not the file."""
     import torch
     n = len(requests)
     rng = np.random.default_rng(seed)
@@ -114,6 +118,27 @@ def serve(requests, images, rate, *, seed=0, voxel_budget=65536, hbm_reserve=4 <
     done = 0
     feats = 93  # the default selection: the benchmark maps
     steps = 0
+    drainer = None
+    drained = []
+    if drain_dir is not None:
+        import concurrent.futures as cf
+        import os
+        os.makedirs(drain_dir, exist_ok=True)
+        drainer = cf.ThreadPoolExecutor(max_workers=drain_workers)
+
+    def drain(i, params, maps):
+        from . import fr_h5_write_maps
+        import os
+        rq = requests[i]
+        img = images[rq.get("image_key", rq["shape"])]
+        mask = rq["mask"]
+        vox = np.flatnonzero(np.asarray(mask).reshape(-1)).astype(np.int32)
+        path = os.path.join(drain_dir, "request_%d.h5" % i)
+        t = time.perf_counter()
+        fr_h5_write_maps(path, params, img, mask, maps, vox, codec=drain_codec,
+                         source_id="request %d" % i, threads=4)
+        return path, time.perf_counter() - t
+
     t0 = time.perf_counter()
     while done < n:
         now = time.perf_counter() - t0
@@ -135,7 +160,7 @@ def serve(requests, images, rate, *, seed=0, voxel_budget=65536, hbm_reserve=4 <
             out = torch.empty((feats, rq["n_voi"]), dtype=torch.float32, device="cuda:%d" % device)
             img = images[rq.get("image_key", rq["shape"])]
             rid = srv.add(p, rq["mask"], img, out)
-            active[rid] = (i, out, est)
+            active[rid] = (i, out, est, p)
             admit_at[i] = time.perf_counter() - t0
             in_use += est
             peak_in_use = max(peak_in_use, in_use)
@@ -147,12 +172,14 @@ def serve(requests, images, rate, *, seed=0, voxel_budget=65536, hbm_reserve=4 <
             if not finished and not (pending and arrivals[pending[0]] <= now):
                 finished = srv.poll(wait=True)
             for rid, st in finished:
-                i, out, est = active.pop(rid)
+                i, out, est, p = active.pop(rid)
                 if st != 0:
                     raise RuntimeError("request %d finished with status %d" % (i, st))
                 latency[i] = time.perf_counter() - t0 - arrivals[i]
                 if keep_outputs:
                     outputs[i] = out
+                if drainer is not None:
+                    drained.append(drainer.submit(drain, i, p, out.cpu().numpy()))
                 srv.release(rid)
                 in_use -= est
                 done += 1
@@ -160,6 +187,10 @@ def serve(requests, images, rate, *, seed=0, voxel_budget=65536, hbm_reserve=4 <
             time.sleep(max(0.0, min(0.01, arrivals[pending[0]] - now)))
     makespan = time.perf_counter() - t0
     srv.close()
+    drain_files = None
+    if drainer is not None:
+        drain_files = [f.result() for f in drained]
+        drainer.shutdown()
     ok = ~np.isnan(latency)
     vf = float(sum(requests[i]["n_voi"] for i in range(n) if ok[i]) * feats)
     stats = {
@@ -173,4 +204,6 @@ def serve(requests, images, rate, *, seed=0, voxel_budget=65536, hbm_reserve=4 <
     }
     if keep_outputs:
         stats["outputs"] = outputs
+    if drain_files is not None:
+        stats["drained"] = drain_files
     return stats

@@ -100,3 +100,32 @@ def test_admission_waits_for_memory():
     stats = serve.serve(reqs, imgs, rate=0.0, seed=2, voxel_budget=20000, hbm_budget=budget)
     assert stats["requests"] == len(reqs)
     assert stats["peak_admitted_bytes"] <= budget
+
+
+def test_served_requests_drain_to_hdf5(tmp_path):
+    # each finished request is written to its own HDF5 file on host threads;
+    # the file's dense maps hold exactly the served values at the VOI voxels
+    import h5read
+
+    import paper_2609_19190_gb300 as fm
+    from paper_2609_19190_gb300 import serve
+    reqs = synth.served_requests(4, seed=9, median=5000.0, max_voxels=30000)
+    imgs = _images(reqs)
+    stats = serve.serve(reqs, imgs, rate=200.0, seed=3, voxel_budget=4000, keep_outputs=True,
+                        drain_dir=str(tmp_path), drain_codec="lzf")
+    assert len(stats["drained"]) == len(reqs)
+    names = fm.fr_feature_names()
+    for i in (0, len(reqs) - 1):
+        rq = reqs[i]
+        f = h5read.File(tmp_path / ("request_%d.h5" % i))
+        vox = np.flatnonzero(rq["mask"].reshape(-1))
+        got = stats["outputs"][i].cpu().numpy()
+        np.testing.assert_array_equal(f.root.members["mask"].data, rq["mask"])
+        np.testing.assert_array_equal(f.root.members["image"].data,
+                                      imgs[rq["shape"]].cpu().numpy())
+        for r in (0, 18, 41, 58, 92):
+            dense = f.root.members["maps"].members[names[r]].data.reshape(-1)
+            np.testing.assert_array_equal(dense[vox].view(np.uint32), got[r].view(np.uint32))
+            outside = np.ones(dense.size, bool)
+            outside[vox] = False
+            assert np.isnan(dense[outside]).all()
