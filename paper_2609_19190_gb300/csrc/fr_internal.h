@@ -29,6 +29,10 @@ constexpr int kBinCap = 64;
 constexpr int kCapL = 12;
 constexpr int kSlot = kCapL * (kCapL + 1) / 2 + 1;  // odd: lanes hit distinct banks
 constexpr int kMaxConsumerWarps = 16;
+// Padded window of the GLDM / NGTDM neighbour pass: sides up to 7 (r <= 3)
+// with a one-voxel zero border.
+constexpr int kPadMaxSide = 7;
+constexpr int kPadCells = (kPadMaxSide + 2) * (kPadMaxSide + 2) * (kPadMaxSide + 2);
 constexpr int kMaxStages = 4;
 // CTA pool of many-level MCC solves: at most one per direction per warp
 constexpr int kFbTasks = kMaxConsumerWarps * kNumDirs;
@@ -160,6 +164,7 @@ struct BigLayout {
   int32_t rhist, rlv, rlen;                  // GLRLM
   int32_t parent, zsz, zlv;                  // GLSZM
   int32_t ghist, gj, ngn, ngs;               // GLDM / NGTDM
+  int32_t ngacc, pad;                        // NGTDM [level][neighbours], padded window
   int32_t bytes;
 };
 
@@ -198,7 +203,9 @@ __host__ __device__ inline BigLayout fr_big_layout(int32_t mc, int32_t bc,
   L.gj = L.ghist + mc * 28 * 4;
   L.ngn = L.gj + 28 * 4;
   L.ngs = fr_align(L.ngn + mc * 4, 8);
-  int32_t gldm_end = L.ngs + mc * 8;
+  L.ngacc = L.ngs + mc * 8;
+  L.pad = L.ngacc + mc * 27 * 4;
+  int32_t gldm_end = L.pad + fr_align(kPadCells * 2, 16);
   int32_t m = glcm_end;
   if (glrlm_end > m) m = glrlm_end;
   if (glszm_end > m) m = glszm_end;

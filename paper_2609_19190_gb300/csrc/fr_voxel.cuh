@@ -40,10 +40,31 @@ namespace fr {
 
 // (dz, dy, dx) of the 13 directions: the vectors of {-1,0,1}^3 that are
 // lexicographically greater than (0,0,0), in increasing order.
-__constant__ signed char c_dirs[13][3] = {
-    {0, 0, 1},  {0, 1, -1}, {0, 1, 0},  {0, 1, 1},  {1, -1, -1},
-    {1, -1, 0}, {1, -1, 1}, {1, 0, -1}, {1, 0, 0},  {1, 0, 1},
-    {1, 1, -1}, {1, 1, 0},  {1, 1, 1}};
+#define FR_DIRECTIONS                                                   \
+  {{0, 0, 1},  {0, 1, -1}, {0, 1, 0},  {0, 1, 1},  {1, -1, -1},          \
+   {1, -1, 0}, {1, -1, 1}, {1, 0, -1}, {1, 0, 0},  {1, 0, 1},            \
+   {1, 1, -1}, {1, 1, 0},  {1, 1, 1}}
+__constant__ signed char c_dirs[13][3] = FR_DIRECTIONS;
+constexpr signed char kDirs[13][3] = FR_DIRECTIONS;
+
+// The same table as 6-bit codes (each component + 1 in two bits), so that
+// lanes working on different directions decode theirs from registers.
+constexpr unsigned long long dir_codes(int lo, int hi) {
+  unsigned long long c = 0;
+  for (int d = hi - 1; d >= lo; --d)
+    c = (c << 6) | (unsigned long long)((kDirs[d][0] + 1) | ((kDirs[d][1] + 1) << 2) |
+                                        ((kDirs[d][2] + 1) << 4));
+  return c;
+}
+constexpr unsigned long long kDirCodesLo = dir_codes(0, 10), kDirCodesHi = dir_codes(10, 13);
+
+__device__ __forceinline__ void dir_of(int di, int& dz, int& dy, int& dx) {
+  const unsigned c =
+      (unsigned)((di < 10 ? kDirCodesLo >> (6 * di) : kDirCodesHi >> (6 * (di - 10))) & 63ull);
+  dz = (int)(c & 3u) - 1;
+  dy = (int)((c >> 2) & 3u) - 1;
+  dx = (int)((c >> 4) & 3u) - 1;
+}
 
 // L / w for w = 0..26 with L = lcm(1..26): s_i * L is then an exact
 // integer sum of |i*w - S| * (L / w).
@@ -209,7 +230,7 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t* a, int lo, int hi
 __device__ __forceinline__ float ent_term(int c, int n) {
   if (c == n) return 0.f;
   const float fc = (float)c, fn = (float)n;
-  return __fdividef(fc, fn) * log2f(__fdividef(fn, fc));
+  return __fdividef(fc, fn) * __log2f(__fdividef(fn, fc));
 }
 
 // ------------------------------------------------------------------ gather
@@ -532,51 +553,27 @@ __host__ __device__ constexpr int pk(int n, int i, int j) {
   return i * n - ((i * (i - 1)) >> 1) + (j - i);
 }
 
-// Sturm counts of the symmetric tridiagonal (d, e2 = squared off-diagonal)
-// times sg (+1 or -1) at K shifts t: c[k] = number of eigenvalues below t[k].
-template <int N, int K>
-__device__ __forceinline__ void sturm_counts(const float (&d)[N], const float (&e2)[N],
-                                             float sg, const float (&t)[K], int (&c)[K]) {
-  float q[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    q[k] = sg * d[0] - t[k];
-    c[k] = q[k] < 0.f;
-  }
+// Sturm count of the symmetric tridiagonal (d, e2 = squared off-diagonal)
+// times sg (+1 or -1) at the shift t: the number of its eigenvalues below t.
+template <int N>
+__device__ __forceinline__ int sturm_count(const float (&d)[N], const float (&e2)[N], float sg,
+                                           float t) {
+  float q = sg * d[0] - t;
+  int c = q < 0.f;
 #pragma unroll
   for (int i = 1; i < N; ++i) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const float qk = fabsf(q[k]) < 1e-30f ? -1e-30f : q[k];
-      q[k] = sg * d[i] - t[k] - __fdividef(e2[i - 1], qk);
-      c[k] += q[k] < 0.f;
-    }
+    const float qk = fabsf(q) < 1e-30f ? -1e-30f : q;
+    q = sg * d[i] - t - __fdividef(e2[i - 1], qk);
+    c += q < 0.f;
   }
+  return c;
 }
 
-// New bracket [lo, hi] of the largest eigenvalue from the counts at the
-// three inner points of a 4-way split (largest < t iff every eigenvalue is).
-// New bracket [lo, hi] of the largest eigenvalue from the counts at the K
-// inner points of a (K + 1)-way split (largest < t iff every eigenvalue is).
-template <int N, int K>
-__device__ __forceinline__ void narrow_top(const float (&t)[K], const int (&c)[K],
-                                           float& lo, float& hi) {
-  float nlo = t[K - 1], nhi = hi;
-#pragma unroll
-  for (int k = K - 1; k >= 0; --k)
-    if (c[k] == N) {
-      nhi = t[k];
-      nlo = k ? t[k - 1] : lo;
-    }
-  lo = nlo;
-  hi = nhi;
-}
-
-// Shifts per bisection round of the per-lane MCC solve ((K + 1)-way split):
-// plain bisection needs the fewest Sturm sequences per bit (the solve is
-// bound by issue slots, not latency: 3 shifts were 2.5 %, 7 shifts 18 %
-// slower on the CT map).
-constexpr int kMccShifts = 1;
+// Rounds of the paired MCC solve: both-ends bisection (one bit per round),
+// then trisection of the deciding end (log2 3 bits per round); about 22 bits
+// in all.
+constexpr int kMccRounds1 = 22;
+constexpr int kMccRounds2 = 14;
 
 // Largest |eigenvalue| of a symmetric N x N matrix read from a packed upper
 // triangle in the kCapL x kCapL layout, by one thread with every value in
@@ -584,10 +581,14 @@ constexpr int kMccShifts = 1;
 // the eigenvalue 0, which every deflated matrix A = S - u u^T already has
 // (A u = 0), so the radius is unchanged and one fixed N serves all smaller
 // matrices.  Householder tridiagonalisation (indices are compile-time
-// constants, so the loops unroll into independent FMAs), then 4-ary Sturm
-// bisection of the two ends of the spectrum.
+// constants, so the loops unroll into independent FMAs), then Sturm
+// bisection of the two ends of the spectrum.  Two lanes solve each matrix
+// (h = 0, 1; pm = the pair's lane mask) and share every round's result: while
+// both ends are open, lane 0 bisects the top end and lane 1 the bottom one;
+// then the pair trisects the deciding end, one shift each.  Both lanes end
+// with the same bracket and return the same value.
 template <int N>
-__device__ __forceinline__ float rho_reg(const float* __restrict__ P) {
+__device__ __forceinline__ float rho_reg(const float* __restrict__ P, int h, unsigned pm) {
   constexpr int NP = N * (N + 1) / 2;
   float a[NP];
 #pragma unroll
@@ -655,42 +656,40 @@ __device__ __forceinline__ float rho_reg(const float* __restrict__ P) {
   // [max d_i, bnd], lambda_min in [-bnd, min d_i], by interlacing) until the
   // brackets show which end decides the radius, then refine that end alone.
   float hl = fmaxf(dmax, 0.f), hh = bnd, ll = -bnd, lh = fminf(dmin, 0.f);
-  constexpr int K = kMccShifts;
-  constexpr float kInv = 1.f / (float)(K + 1);
-  constexpr int kRounds = K == 1 ? 22 : K == 3 ? 11 : K == 7 ? 8 : 11;  // ~22 bits
   int it = 0;
-  for (; it < kRounds; ++it) {
+  for (; it < kMccRounds1; ++it) {
     if (hl >= -ll || -lh >= hh) break;  // one end dominates
-    float th[K], tl[K];
-    int ch[K], cl[K];
-    const float hs = kInv * (hh - hl), ls = kInv * (lh - ll);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      th[k] = hl + hs * (float)(k + 1);
-      tl[k] = -lh + ls * (float)(k + 1);  // shifts of -A: -lambda_min is its largest
-    }
-    sturm_counts<N, K>(d, e2, 1.f, th, ch);
-    sturm_counts<N, K>(d, e2, -1.f, tl, cl);
-    narrow_top<N, K>(th, ch, hl, hh);
-    float nl = -lh, nh = -ll;
-    narrow_top<N, K>(tl, cl, nl, nh);
-    lh = -nl;
-    ll = -nh;
+    // lane 0: top bracket [hl, hh] of A; lane 1: top bracket [-lh, -ll] of -A
+    const float lo = h ? -lh : hl, hi = h ? -ll : hh;
+    const float t = 0.5f * (lo + hi);
+    const bool below = sturm_count<N>(d, e2, h ? -1.f : 1.f, t) == N;  // every eigenvalue < t
+    const float nlo = below ? lo : t, nhi = below ? t : hi;
+    const float olo = __shfl_xor_sync(pm, nlo, 16), ohi = __shfl_xor_sync(pm, nhi, 16);
+    hl = h ? olo : nlo;
+    hh = h ? ohi : nhi;
+    lh = -(h ? nlo : olo);
+    ll = -(h ? nhi : ohi);
   }
-  if (it == kRounds) return fmaxf(fabsf(0.5f * (hl + hh)), fabsf(0.5f * (ll + lh)));
+  if (it == kMccRounds1) return fmaxf(fabsf(0.5f * (hl + hh)), fabsf(0.5f * (ll + lh)));
   const bool top = hl >= -ll;
   const float sg = top ? 1.f : -1.f;
   float lo = top ? hl : -lh, hi = top ? hh : -ll;
-  for (; it < kRounds; ++it) {
+  for (int r = 0; r < kMccRounds2; ++r) {
     // the bracket is fine enough: half-width <= max(5e-7, 1e-5 lambda)
     if (hi - lo <= fmaxf(1e-6f, 2e-5f * lo)) break;
-    float t[K];
-    int c[K];
-    const float st = kInv * (hi - lo);
-#pragma unroll
-    for (int k = 0; k < K; ++k) t[k] = lo + st * (float)(k + 1);
-    sturm_counts<N, K>(d, e2, sg, t, c);
-    narrow_top<N, K>(t, c, lo, hi);
+    const float st = (hi - lo) * (1.f / 3.f);
+    const float t1 = lo + st, t2 = lo + 2.f * st;
+    const int c = sturm_count<N>(d, e2, sg, h ? t2 : t1);
+    const int co = __shfl_xor_sync(pm, c, 16);
+    const int c1 = h ? co : c, c2 = h ? c : co;
+    if (c1 == N) {
+      hi = t1;
+    } else if (c2 == N) {
+      lo = t1;
+      hi = t2;
+    } else {
+      lo = t2;
+    }
   }
   return 0.5f * (lo + hi);
 }
@@ -790,17 +789,74 @@ __device__ __forceinline__ void slice_masks(const Win& w, const Arena& A,
   }
 }
 
-// (1 + d) ln(1 + d) - d >= 0 (d >= -1) without the cancellation near d = 0:
-// there its Taylor series sum_{k>=2} (-d)^k / (k (k - 1)), cut after d^9.
+// Warp sum of K <= 16 values per lane, scattered: lane L receives the total
+// of v[L >> 1] (zero for L >> 1 >= K).  Recursive halving: at offset o a lane
+// keeps the half of its partial sums selected by its bit o and sends the
+// other half, so 16 sums cost 15 exchanges instead of 80.
+template <int K>
+__device__ __forceinline__ float warp_rsum_f32(const float (&v)[K]) {
+  static_assert(K <= 16, "at most 16 sums");
+  const int lane = lane_id();
+  float x[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = k < K ? v[k] : 0.f;
+#pragma unroll
+  for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = up ? x[i] : x[i + h];
+      const float keep = up ? x[i + h] : x[i];
+      x[i] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+  return x[0] + __shfl_xor_sync(kFull, x[0], 1);
+}
+
+// Which of the 12 GLCM per-direction sums the feature of lane L reads
+// (4 bits per lane; 0 where none): Autocorrelation .. SumEntropy order.
+constexpr unsigned long long kGlcmSumLo =  // lanes 0..15
+    (11ull << (4 * 2)) | (10ull << (4 * 4)) | (3ull << (4 * 8)) | (1ull << (4 * 11)) |
+    (2ull << (4 * 12)) | (2ull << (4 * 13)) | (4ull << (4 * 14)) | (5ull << (4 * 15));
+constexpr unsigned long long kGlcmSumHi =  // lanes 16..31
+    (6ull << (4 * 0)) | (7ull << (4 * 1)) | (8ull << (4 * 2)) | (9ull << (4 * 5));
+__device__ __forceinline__ int glcm_sum_of_lane(int lane) {
+  return (int)((lane < 16 ? kGlcmSumLo >> (4 * lane) : kGlcmSumHi >> (4 * (lane - 16))) & 15ull);
+}
+
+// Pair t (0 <= t < m (m + 1) / 2) of the packed upper triangle of an m x m
+// matrix as its row a and column b >= a: row a starts at a m - a (a - 1) / 2.
+__device__ __forceinline__ void pair_of(int t, int m, int& a, int& b) {
+  const float q = (float)(2 * m + 1);
+  a = (int)((q - sqrtf(q * q - 8.f * (float)t)) * 0.5f);
+  a = max(0, min(a, m - 1));
+  while (a + 1 < m && (a + 1) * m - (((a + 1) * a) >> 1) <= t) ++a;
+  while (a > 0 && a * m - ((a * (a - 1)) >> 1) > t) --a;
+  b = a + (t - (a * m - ((a * (a - 1)) >> 1)));
+}
+
+// (1 + d) ln(1 + d) - d >= 0 (d > -1) without the cancellation near d = 0:
+// for |d| < 1/4 its Taylor series sum_{k>=2} (-d)^k / (k (k - 1)), cut after
+// d^13 (the next term is below 1e-9 of the sum); beyond, the hardware log2
+// (absolute error ~1e-7 near 1, where the result is > 0.02).
 __device__ __forceinline__ float kl_term(float d) {
-  if (fabsf(d) < 0.125f)
-    return d * d *
-           (0.5f + d * (-1.f / 6.f +
-                        d * (1.f / 12.f +
-                             d * (-1.f / 20.f +
-                                  d * (1.f / 30.f +
-                                       d * (-1.f / 42.f + d * (1.f / 56.f + d * (-1.f / 72.f))))))));
-  return (1.f + d) * log1pf(d) - d;
+  if (fabsf(d) < 0.25f) {
+    float s = -1.f / 156.f;
+    s = fmaf(s, d, 1.f / 132.f);
+    s = fmaf(s, d, -1.f / 110.f);
+    s = fmaf(s, d, 1.f / 90.f);
+    s = fmaf(s, d, -1.f / 72.f);
+    s = fmaf(s, d, 1.f / 56.f);
+    s = fmaf(s, d, -1.f / 42.f);
+    s = fmaf(s, d, 1.f / 30.f);
+    s = fmaf(s, d, -1.f / 20.f);
+    s = fmaf(s, d, 1.f / 12.f);
+    s = fmaf(s, d, -1.f / 6.f);
+    s = fmaf(s, d, 0.5f);
+    return d * d * s;
+  }
+  const float x = 1.f + d;
+  return fmaf(x * __log2f(x), 0.69314718055994531f, -d);
 }
 
 // ------------------------------------------------------------------ GLCM
@@ -830,12 +886,18 @@ static __device__ void glcm_finish(const Arena& A, const FrJob& job) {
   __syncwarp();
   if (want_mcc) {
     // one register-resident size for the warp: the smallest that holds every
-    // direction's matrix (zero padding leaves the radius unchanged)
-    const int nl = (lane < kNumDirs) ? mn[lane] : 0;
+    // direction's matrix (zero padding leaves the radius unchanged); lanes d
+    // and d + 16 solve direction d together
+    const int dl = lane & 15, h = lane >> 4;
+    const int nl = (dl < kNumDirs) ? mn[dl] : 0;
     const int nmax = __reduce_max_sync(kFull, nl);
     if (nl >= 2) {
-      const float* P = slots + lane * kSlot;
-      mres[lane] = nmax <= 4 ? rho_reg<4>(P) : nmax <= 8 ? rho_reg<8>(P) : rho_reg<kCapL>(P);
+      const float* P = slots + dl * kSlot;
+      const unsigned pm = (1u << dl) | (1u << (dl + 16));
+      const float r = nmax <= 4   ? rho_reg<4>(P, h, pm)
+                      : nmax <= 8 ? rho_reg<8>(P, h, pm)
+                                  : rho_reg<kCapL>(P, h, pm);
+      if (!h) mres[dl] = r;
     }
     __syncwarp();
     if (lane == 23) {
@@ -921,6 +983,18 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
   W Lm[SS], Vm[SS];
   if constexpr (S > 0) slice_masks<S>(w, A, Lm, Vm);
   const int npairs = m * (m + 1) / 2;
+  // this lane's level pair in the first two rounds of the pair loop (the
+  // same for every direction), 5 bits per level: a0 b0 a1 b1
+  unsigned pairs01 = 0;
+  if constexpr (S > 0) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int t = 32 * r + lane;
+      int a = 0, b = 0;
+      if (t < npairs) pair_of(t, m, a, b);
+      pairs01 |= (unsigned)(a | (b << 5)) << (10 * r);
+    }
+  }
   int np = 0;
   for (int di = 0; di < kNumDirs; ++di) {
     const int ddz = c_dirs[di][0] * job.delta, ddy = c_dirs[di][1] * job.delta,
@@ -1051,13 +1125,13 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
         const bool valid = t < npairs;
         int a = 0, b = 0;
         if (valid) {
-          // row a of the packed upper triangle: start(a) = a m - a (a - 1) / 2
-          const float q = (float)(2 * m + 1);
-          a = (int)((q - sqrtf(q * q - 8.f * (float)t)) * 0.5f);
-          a = max(0, min(a, m - 1));
-          while (a + 1 < m && (a + 1) * m - (((a + 1) * a) >> 1) <= t) ++a;
-          while (a > 0 && a * m - ((a * (a - 1)) >> 1) > t) --a;
-          b = a + (t - (a * m - ((a * (a - 1)) >> 1)));
+          if (t0 < 64) {
+            const unsigned pr = pairs01 >> (10 * (t0 >> 5));
+            a = (int)(pr & 31u);
+            b = (int)((pr >> 5) & 31u);
+          } else {
+            pair_of(t, m, a, b);
+          }
         }
         int n = 0;
 #pragma unroll
@@ -1262,39 +1336,38 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
     sk2 = merged ? warp_sum_u64(sk2) : redux_u32((unsigned)sk2);
     sk = redux_u32(sk);
     ce3 = warp_sum_i128(ce3);
-    float fs[12] = {hx, hxy, mi, de, idm, idmn, idd, idn, iv, se, ce2, ce4};
-    warp_sum_f32x<12>(fs);
-    fs[2] = (fs[2] + __fdividef((float)mi0, fT2)) * 1.44269504088896341f;  // bits
+    const float fs[12] = {hx, hxy, mi, de, idm, idmn, idd, idn, iv, se, ce2, ce4};
+    // lanes 2k, 2k + 1 hold the total of fs[k]; MI (k = 2) in bits
+    float tot = warp_rsum_f32<12>(fs);
+    if ((lane >> 1) == 2) tot = (tot + __fdividef((float)mi0, fT2)) * 1.44269504088896341f;
+    const float fa = __shfl_sync(kFull, tot, 2 * glcm_sum_of_lane(lane));  // this lane's sum
+    const float f0 = __shfl_sync(kFull, tot, 0);                            // HX
     // one lane per feature
     float num = kNaNf, den = 1.f;
     const long long var_num = (long long)T * (long long)m2 - (long long)m1 * m1;  // T^2 sigma^2
     if (lane == 0) { num = (float)a1; den = fT; }
     if (lane == 1) { num = (float)m1; den = fT; }
-    if (lane == 2) { num = fs[11]; den = fT * fT * fT * fT * fT; }
+    if (lane == 2) { num = fa; den = fT * fT * fT * fT * fT; }
     if (lane == 3) {
       num = i128_to_f32(ce3);
       den = fT * fT * fT * fT;
       csn[ds] = i128_to_f64(ce3);
       cst[ds] = T;
     }
-    if (lane == 4) { num = fs[10]; den = fT * fT * fT; }
+    if (lane == 4) { num = fa; den = fT * fT * fT; }
     if (lane == 5) { num = (float)dk2; den = fT; }
     if (lane == 6) { num = (float)((long long)T * (long long)a1 - (long long)m1 * m1); den = (float)var_num; }
     if (lane == 7) { num = (float)dk; den = fT; }
-    if (lane == 8) { num = fs[3]; }
+    if (lane == 8) { num = fa; }
     if (lane == 9) { num = (float)((long long)T * (long long)dk2 - (long long)dk * dk); den = fT * fT; }
     if (lane == 10) { num = (float)e2; den = fT * fT; }
-    if (lane == 11) { num = fs[1]; }
-    if (lane == 12) { num = -fs[2]; den = fs[0]; }
-    if (lane == 13) { num = sqrtf(fmaxf(0.f, -expm1f(-2.f * fs[2]))); }
-    if (lane == 14) { num = fs[4]; den = fT; }
-    if (lane == 15) { num = fs[5]; den = fT; }
-    if (lane == 16) { num = fs[6]; den = fT; }
-    if (lane == 17) { num = fs[7]; den = fT; }
-    if (lane == 18) { num = fs[8]; den = fT; }
+    if (lane == 11) { num = fa; }
+    if (lane == 12) { num = -fa; den = f0; }
+    if (lane == 13) { num = sqrtf(fmaxf(0.f, -expm1f(-2.f * fa))); }
+    if (lane >= 14 && lane <= 18) { num = fa; den = fT; }
     if (lane == 19) { num = (float)maxc; den = fT; }
     if (lane == 20) { num = (float)sk; den = fT; }
-    if (lane == 21) { num = fs[9]; }
+    if (lane == 21) { num = fa; }
     if (lane == 22) { num = (float)var_num; den = fT * fT; }
     // IBSI extras (lanes 24, 25): sum variance, dissimilarity
     if (lane == 24) { num = (float)((long long)T * (long long)sk2 - (long long)sk * sk); den = fT * fT; }
@@ -1466,10 +1539,178 @@ __device__ void glrlm_masks(const Win& w, const Arena& A, bool merged, int32_t* 
   acc_store(A, 16, 42);
 }
 
+// GLRLM feature f (0..15) of one direction from its run totals; NaN where
+// the denominator is 0.  Every lane evaluates the chain for its own f.
+__device__ __forceinline__ float glrlm_feature(int f, const float (&fsr)[7], unsigned nr,
+                                               unsigned sj2, unsigned glnu, unsigned rlnu,
+                                               unsigned si, unsigned si2, unsigned sj, float nvf) {
+  const float N = (float)nr;
+  float num = kNaNf, den = N;
+  if (f == 0) { num = fsr[0]; }
+  if (f == 1) { num = (float)sj2; }
+  if (f == 2) { num = (float)glnu; }
+  if (f == 3) { num = (float)glnu; den = N * N; }
+  if (f == 4) { num = (float)rlnu; }
+  if (f == 5) { num = (float)rlnu; den = N * N; }
+  if (f == 6) { num = N; den = nvf; }
+  if (f == 7) { num = (float)((long long)nr * si2 - (long long)si * si); den = N * N; }
+  if (f == 8) { num = (float)((long long)nr * sj2 - (long long)sj * sj); den = N * N; }
+  if (f == 9) { num = fsr[6]; den = 1.f; }
+  if (f == 10) { num = fsr[1]; }
+  if (f == 11) { num = (float)si2; }
+  if (f == 12) { num = fsr[2]; }
+  if (f == 13) { num = fsr[3]; }
+  if (f == 14) { num = fsr[4]; }
+  if (f == 15) { num = fsr[5]; }
+  return lane_quot(num, den);
+}
+
+// Compensated (TwoSum) accumulation of one value, and the merge of two such
+// partial sums.
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float v) {
+  const float t = s + v, bv = t - s;
+  c += (s - (t - bv)) + (v - bv);
+  s = t;
+}
+
+// GLRLM (per-direction aggregation) of windows of side S <= 5 with at most
+// 16 levels: the warp splits into segments of Wd = 8 or 16 lanes, one
+// direction per segment and one level per lane, so a pass covers 32 / Wd
+// directions (4 or 2) instead of one.  Run counts as in glrlm_masks; the
+// per-direction totals are segment reductions; each lane finishes 16 / Wd of
+// the direction's features and keeps their direction sums (compensated) in
+// registers; the segments' sums are merged at the end.
+template <int S>
+__device__ void glrlm_masks_packed(const Win& w, const Arena& A, int32_t* dbg_glrlm) {
+  using W = typename SliceT<S>::W;
+  const int lane = lane_id();
+  W L0[S], V[S];
+  slice_masks<S>(w, A, L0, V);
+  (void)V;
+  const int m = w.m;
+  const int Wd = m <= 8 ? 8 : 16;
+  const int G = 32 / Wd;
+  const int sl = lane & (Wd - 1), g = lane / Wd;
+  const unsigned segmask = ((1u << Wd) - 1u) << (g * Wd);
+  const bool ok = sl < m;
+  W L[S];
+#pragma unroll
+  for (int z = 0; z < S; ++z) {
+    const W v = __shfl_sync(kFull, L0[z], sl);
+    L[z] = ok ? v : (W)0;
+  }
+  const unsigned i = ok ? (unsigned)A.lev[sl] : 1u;
+  const float fi2 = (float)(i * i), inv_i2 = __fdividef(1.f, fi2);
+  const float nvf = (float)w.nv;
+  float as[2] = {0.f, 0.f}, ac[2] = {0.f, 0.f};
+  int an[2] = {0, 0};
+  for (int d0 = 0; d0 < kNumDirs; d0 += G) {
+    const int di = d0 + g;
+    const bool dok = di < kNumDirs;
+    int dz, dy, dx;
+    dir_of(dok ? di : 0, dz, dy, dx);
+    const SliceDir<S> D(dz, dy, dx);
+    W st[S], R[S], T[S];
+    D.bwd(L, T);
+    unsigned c[S + 1];
+    c[0] = 0u;
+#pragma unroll
+    for (int z = 0; z < S; ++z) {
+      st[z] = L[z] & ~T[z];
+      R[z] = L[z];
+      c[0] += (unsigned)popc_w<W>(st[z]);
+    }
+#pragma unroll
+    for (int j = 1; j < S; ++j) {
+      D.fwd(R, T);
+      c[j] = 0u;
+#pragma unroll
+      for (int z = 0; z < S; ++z) {
+        R[z] = L[z] & T[z];
+        c[j] += (unsigned)popc_w<W>(st[z] & R[z]);
+      }
+    }
+    c[S] = 0u;
+    unsigned h[S];
+    unsigned row = 0, sj = 0, sj2 = 0;
+    float fs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sre lgl srl srh lrl lrh
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const unsigned cnt = c[j] - c[j + 1];  // runs of length j + 1
+      h[j] = cnt;
+      const unsigned J = (unsigned)(j + 1);
+      const float fc = (float)cnt, fj2 = (float)(J * J), inv_j2 = 1.f / (float)(J * J);
+      row += cnt;
+      sj += cnt * J;
+      sj2 += cnt * J * J;
+      fs[0] += fc * inv_j2;
+      fs[1] += fc * inv_i2;
+      fs[2] += fc * inv_i2 * inv_j2;
+      fs[3] += fc * fi2 * inv_j2;
+      fs[4] += fc * fj2 * inv_i2;
+      fs[5] += fc * fi2 * fj2;
+      if (dbg_glrlm && cnt && dok)
+        dbg_glrlm[((size_t)di * w.ng + (i - 1)) * w.s + j] = (int)cnt;
+    }
+    const unsigned nr = __reduce_add_sync(segmask, row);
+    unsigned rlnu = 0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const unsigned col = __reduce_add_sync(segmask, h[j]);
+      rlnu += col * col;
+    }
+    float ent = 0.f;
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+      if (h[j]) ent += ent_term((int)h[j], (int)nr);
+    const unsigned glnu = __reduce_add_sync(segmask, row * row);
+    const unsigned si = __reduce_add_sync(segmask, row * i);
+    const unsigned si2 = __reduce_add_sync(segmask, row * i * i);
+    const unsigned sjt = __reduce_add_sync(segmask, sj);
+    const unsigned sj2t = __reduce_add_sync(segmask, sj2);
+    float fsr[7] = {fs[0], fs[1], fs[2], fs[3], fs[4], fs[5], ent};
+    for (int o = Wd >> 1; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < 7; ++k) fsr[k] += __shfl_xor_sync(kFull, fsr[k], o);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int f = sl + k * Wd;
+      if (f < 16) {
+        const float v = glrlm_feature(f, fsr, nr, sj2t, glnu, rlnu, si, si2, sjt, nvf);
+        if (dok && !isnan(v)) {
+          two_sum_add(as[k], ac[k], v);
+          ++an[k];
+        }
+      }
+    }
+  }
+  // merge the segments' direction sums
+  for (int o = Wd; o < 32; o <<= 1)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float so = __shfl_xor_sync(kFull, as[k], o), co = __shfl_xor_sync(kFull, ac[k], o);
+      const int no = __shfl_xor_sync(kFull, an[k], o);
+      two_sum_add(as[k], ac[k], so);
+      ac[k] += co;
+      an[k] += no;
+    }
+  if (g == 0)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int f = sl + k * Wd;
+      if (f < 16) A.fv[42 + f] = an[k] ? __fdividef(as[k] + ac[k], (float)an[k]) : kNaNf;
+    }
+  __syncwarp();
+}
+
 // merged: the 13 directions' runs go into one matrix, whose features are
 // taken once (RunPercentage over 13 N_v: each voxel lies on one run per
 // direction).
 static __device__ void glrlm_family(const Win& w, const Arena& A, bool merged, int32_t* dbg_glrlm) {
+  if (!merged && w.m <= 16) {
+    if (w.s == 3) return glrlm_masks_packed<3>(w, A, dbg_glrlm);
+    if (w.s == 5) return glrlm_masks_packed<5>(w, A, dbg_glrlm);
+  }
   if (w.m <= 32) {
     if (w.s == 3) return glrlm_masks<3>(w, A, merged, dbg_glrlm);
     if (w.s == 5) return glrlm_masks<5>(w, A, merged, dbg_glrlm);
@@ -1895,6 +2136,81 @@ static __device__ void glszm_family(const Win& w, const Arena& A, int32_t* dbg_g
 }
 
 // ------------------------------------------------------------------ GLDM + NGTDM
+// Neighbour pass of windows of side S <= 7 on a padded copy: cell
+// ((z+1) P + y+1) P + x+1 (P = S + 2) holds the compact level a | gray level
+// << 8 of each VOI voxel, 0 elsewhere (the border too), so the 26 neighbour
+// reads are unconditional with compile-time offsets.  GLDM counts go to
+// gh[a][k]; NGTDM per (level, neighbour count w) to ngacc as one 32-bit word,
+// count << 22 | sum of |i w - S| (per cell: count <= 343, sum < 2^22), which
+// the caller turns into n_i and s_i L (clearing them).  The padded copy and
+// ngacc share bytes with regions the GLCM family leaves non-zero (its MCC
+// slots), so both are cleared here first; the copy is cleared again on exit.
+template <int S>
+__device__ void gldm_ngtdm_pass_padded(const Win& w, const Arena& A, bool do_gldm,
+                                       bool do_ngtdm) {
+  constexpr int P = S + 2, P2 = P * P, S3 = S * S * S;
+  const int lane = lane_id();
+  uint16_t* pad = (uint16_t*)(A.big + A.L.pad);
+  int* gh = (int*)(A.big + A.L.ghist);
+  unsigned* ngacc = (unsigned*)(A.big + A.L.ngacc);
+  for (int t = lane; t < (P * P2 + 1) / 2; t += 32) ((unsigned*)pad)[t] = 0u;
+  if (do_ngtdm)
+    for (int t = lane; t < w.m * 27; t += 32) ngacc[t] = 0u;
+  __syncwarp();
+  for (int p = lane; p < S3; p += 32) {
+    const int a = A.lvl[p];
+    if (a) {
+      const int z = p / (S * S), y = (p / S) % S, x = p % S;
+      pad[((z + 1) * P + y + 1) * P + x + 1] = (uint16_t)(a | ((int)A.lev[a - 1] << 8));
+    }
+  }
+  __syncwarp();
+  for (int base = 0; base < S3; base += 32) {
+    const int p = base + lane;
+    int key = -1;
+    if (p < S3) {
+      const int z = p / (S * S), y = (p / S) % S, x = p % S;
+      const uint16_t* c = pad + ((z + 1) * P + y + 1) * P + x + 1;
+      const unsigned v = *c;
+      const int a = (int)(v & 0xFFu);
+      if (a) {
+        int keq = 0, nw = 0, ssum = 0;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+              if (!dz && !dy && !dx) continue;
+              const unsigned u = c[dz * P2 + dy * P + dx];
+              const int b = (int)(u & 0xFFu);
+              nw += b != 0;
+              ssum += (int)(u >> 8);
+              keq += b == a;
+            }
+        key = (a - 1) * 28 + keq;
+        if (do_ngtdm && nw > 0) {
+          const int dlt = abs((int)(v >> 8) * nw - ssum);
+          atomicAdd(&ngacc[(a - 1) * 27 + nw], (unsigned)dlt + (1u << 22));
+        }
+      }
+    }
+    if (do_gldm) {
+      const unsigned act = __ballot_sync(kFull, key >= 0);
+      if (key >= 0) {
+        const unsigned grp = __match_any_sync(act, key);
+        if ((grp & lanemask_lt()) == 0) atomicAdd(&gh[key], __popc(grp));
+      }
+    }
+  }
+  __syncwarp();
+  for (int p = lane; p < S3; p += 32)  // leave the padded copy zero
+    if (A.lvl[p]) {
+      const int z = p / (S * S), y = (p / S) % S, x = p % S;
+      pad[((z + 1) * P + y + 1) * P + x + 1] = 0;
+    }
+}
+
 static __device__ void gldm_ngtdm_family(const Win& w, const Arena& A, const FrJob& job,
                                   int32_t* dbg_gldm, int32_t* dbg_ngn,
                                   long long* dbg_ngs) {
@@ -1906,7 +2222,29 @@ static __device__ void gldm_ngtdm_family(const Win& w, const Arena& A, const FrJ
   int* gj = (int*)(A.big + A.L.gj);
   int* ngn = (int*)(A.big + A.L.ngn);
   unsigned long long* ngs = (unsigned long long*)(A.big + A.L.ngs);
-  for (int base = 0; base < w.W; base += 32) {
+  if (w.s == 3 || w.s == 5 || w.s == 7) {
+    if (w.s == 3) gldm_ngtdm_pass_padded<3>(w, A, do_gldm, do_ngtdm);
+    if (w.s == 5) gldm_ngtdm_pass_padded<5>(w, A, do_gldm, do_ngtdm);
+    if (w.s == 7) gldm_ngtdm_pass_padded<7>(w, A, do_gldm, do_ngtdm);
+    if (do_ngtdm) {
+      // n_i and s_i L from the (level, neighbour count) words
+      unsigned* ngacc = (unsigned*)(A.big + A.L.ngacc);
+      for (int a = lane; a < m; a += 32) {
+        unsigned n = 0;
+        unsigned long long sl = 0;
+        for (int k = 1; k <= 26; ++k) {
+          const unsigned c = ngacc[a * 27 + k];
+          if (!c) continue;
+          ngacc[a * 27 + k] = 0;
+          n += c >> 22;
+          sl += (unsigned long long)(c & 0x3FFFFFu) * (unsigned long long)c_ldiv.v[k];
+        }
+        ngn[a] = (int)n;
+        ngs[a] = sl;
+      }
+    }
+  }
+  for (int base = 0; w.s != 3 && w.s != 5 && w.s != 7 && base < w.W; base += 32) {
     const int p = base + lane;
     int key = -1;
     if (p < w.W) {
