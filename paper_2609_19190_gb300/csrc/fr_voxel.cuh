@@ -428,6 +428,13 @@ __device__ __forceinline__ void acc_lane(const Arena& A, int nf, float v) {
     A.nacc[lane] += 1;
   }
 }
+// Compensated (TwoSum) accumulation of one value into (s, c).
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float v) {
+  const float t = s + v, bv = t - s;
+  c += (s - (t - bv)) + (v - bv);
+  s = t;
+}
+
 __device__ __forceinline__ void acc_store(const Arena& A, int nf, int f0) {
   __syncwarp();
   const int lane = lane_id();
@@ -1418,9 +1425,310 @@ static __device__ void fb_pool_work(const FbPool& P, const FrMapArgs& args, int 
 
 // pool: many-level MCC solves go to the CTA pool (windows in shared memory);
 // null solves them inline.  The caller runs glcm_finish after the pool.
+// GLCM of windows of side S in {3, 5, 7} with at most kDirLevels levels
+// (distance 1, per-direction aggregation): lane d < 13 takes direction d
+// through every step on its own -- pair counts from the level sets, the
+// entry sums, the difference and sum distributions, the 26 per-direction
+// features and its MCC slot -- so no step needs a warp reduction; the
+// direction means are then taken per feature in direction order.  The
+// distributions are kept per direction over the voxel's distinct gray-level
+// differences and sums (at most one per level pair), numbered once per
+// voxel from bit masks of the values present.
+constexpr int kDirLevels = 9;
+constexpr int kDirPairs = kDirLevels * (kDirLevels + 1) / 2;  // 45
+constexpr int kDirRow = 46;  // u16 per distribution row (23 words: odd stride)
+
+template <int S>
+__device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
+                               int32_t* dbg_glcm) {
+  using W = typename SliceT<S>::W;
+  const int lane = lane_id();
+  const int m = w.m;
+  const int npairs = m * (m + 1) / 2;
+  const bool want_mcc = (job.families & kFamMCC) != 0;
+  // layout (this path uses none of the count-matrix path's arrays below
+  // byte 3648, and leaves every byte it uses zero)
+  W* Lsm = (W*)A.big;                                      // [kDirLevels][S]
+  uint16_t* mg = (uint16_t*)(A.big + 512);                 // [13][10] marginals
+  uint16_t* hk = (uint16_t*)(A.big + 776);                 // [13][kDirRow] by difference
+  uint16_t* hs = hk + 13 * kDirRow;                        // [13][kDirRow] by sum
+  uint16_t* pinfo = hs + 13 * kDirRow;                     // [kDirPairs] class ids
+  uint8_t* kval = (uint8_t*)(pinfo + 48);                  // difference of each class
+  uint8_t* sval = kval + 48;                               // sum - 2 lev0 of each class
+  float* fvd = (float*)hk;                                 // [13][27] after the bins
+  int* mn = (int*)(A.big + A.L.mn);
+  float* mres = (float*)(A.big + A.L.mres);
+  float* slots = (float*)(A.big + A.L.slots);
+  double* csn = (double*)(A.big + A.L.csn);
+  int* cst = (int*)(A.big + A.L.cst);
+  acc_reset(A);
+  W Lm[S], Vm[S];
+  slice_masks<S>(w, A, Lm, Vm);
+  if (lane < m)
+#pragma unroll
+    for (int z = 0; z < S; ++z) Lsm[lane * S + z] = Lm[z];
+  // difference / sum classes of the level pairs: bit masks of the values
+  // present (difference < 64, sum - 2 lev0 < 128), class = rank of the value
+  unsigned km[2] = {0u, 0u}, sm4[4] = {0u, 0u, 0u, 0u};
+  int pk_[2] = {0, 0}, ps_[2] = {0, 0};
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int t = 32 * r + lane;
+    if (t < npairs) {
+      int a, b;
+      pair_of(t, m, a, b);
+      const int k = (int)A.lev[b] - (int)A.lev[a];
+      const int sm_ = (int)A.lev[a] + (int)A.lev[b] - 2 * w.lev0;
+      pk_[r] = k;
+      ps_[r] = sm_;
+      km[k >> 5] |= 1u << (k & 31);
+      sm4[sm_ >> 5] |= 1u << (sm_ & 31);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) km[q] = __reduce_or_sync(kFull, km[q]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sm4[q] = __reduce_or_sync(kFull, sm4[q]);
+  const int nk = __popc(km[0]) + __popc(km[1]);
+  const int ns = __popc(sm4[0]) + __popc(sm4[1]) + __popc(sm4[2]) + __popc(sm4[3]);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int t = 32 * r + lane;
+    if (t < npairs) {
+      const int k = pk_[r], sm_ = ps_[r];
+      int kid = __popc(km[0] & ((k >= 32) ? ~0u : ((1u << (k & 31)) - 1u)));
+      if (k >= 32) kid += __popc(km[1] & ((1u << (k & 31)) - 1u));
+      int sid = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int lo = 32 * q;
+        sid += sm_ >= lo + 32 ? __popc(sm4[q])
+                              : sm_ > lo ? __popc(sm4[q] & ((1u << (sm_ - lo)) - 1u)) : 0;
+      }
+      pinfo[t] = (uint16_t)(kid | (sid << 8));
+      kval[kid] = (uint8_t)k;
+      sval[sid] = (uint8_t)sm_;
+    }
+  }
+  if (lane < kNumDirs) cst[lane] = 0;
+  __syncwarp();
+  if (lane < kNumDirs) {
+    const int d = lane;
+    int dz, dy, dx;
+    dir_of(d, dz, dy, dx);
+    const SliceDir<S> D(dz, dy, dx);
+    W fV[S], bV[S];
+    D.fwd(Vm, fV);
+    D.bwd(Vm, bV);
+    unsigned npz = 0;
+#pragma unroll
+    for (int z = 0; z < S; ++z) npz += (unsigned)popc_w<W>(Vm[z] & fV[z]);
+    const int T = 2 * (int)npz;
+    float* row = fvd + d * 27;  // written after the distributions are read
+    float fval[26];
+    if (T == 0) {
+      mn[d] = 0;
+      mres[d] = kNaNf;
+#pragma unroll
+      for (int f = 0; f < 26; ++f) fval[f] = kNaNf;
+    } else {
+      const float fT = (float)T, fT2 = fT * fT, invT = __fdividef(1.f, fT);
+      uint16_t* mrow = mg + d * 10;
+      // marginals c_a = |L_a & fwd(V)| + |L_a & bwd(V)|
+      unsigned m1 = 0, m2 = 0, pmask = 0;
+      float hx = 0.f;
+      for (int a = 0; a < m; ++a) {
+        unsigned c = 0;
+#pragma unroll
+        for (int z = 0; z < S; ++z) {
+          const W la = Lsm[a * S + z];
+          c += (unsigned)(popc_w<W>(la & fV[z]) + popc_w<W>(la & bV[z]));
+        }
+        mrow[a] = (uint16_t)c;
+        if (c) {
+          const unsigned i = A.lev[a];
+          m1 += i * c;
+          m2 += i * i * c;
+          hx += ent_term((int)c, T);
+          pmask |= 1u << a;
+        }
+      }
+      const int present = __popc(pmask);
+      const bool slot = want_mcc && present >= 2;
+      float* P = slots + d * kSlot;
+      if (slot)
+        for (int t = 0; t < kSlot; ++t) P[t] = 0.f;
+      mn[d] = slot ? present : 0;
+      if (!slot) mres[d] = kNaNf;
+      uint16_t* hkr = hk + d * kDirRow;
+      uint16_t* hsr = hs + d * kDirRow;
+      unsigned a1 = 0, e2 = 0, maxc = 0;
+      unsigned long long mi0 = 0;
+      float hxy = 0.f, mi = 0.f;
+      int t = 0;
+      for (int a = 0; a < m; ++a) {
+        W la[S], fa[S], ba[S];
+#pragma unroll
+        for (int z = 0; z < S; ++z) la[z] = Lsm[a * S + z];
+        D.fwd(la, fa);
+        D.bwd(la, ba);
+        const int ca = mrow[a];
+        const unsigned i = A.lev[a];
+        const int pa = __popc(pmask & ((1u << a) - 1u));
+        for (int b = a; b < m; ++b, ++t) {
+          int n = 0;
+          if (b == a) {
+#pragma unroll
+            for (int z = 0; z < S; ++z) n += popc_w<W>(la[z] & fa[z]);
+          } else {
+#pragma unroll
+            for (int z = 0; z < S; ++z) {
+              const W lb = Lsm[b * S + z];
+              n += popc_w<W>(lb & fa[z]) + popc_w<W>(lb & ba[z]);
+            }
+          }
+          const int cb = mrow[b];
+          if (!ca || !cb) continue;
+          const unsigned mult = (a == b) ? 1u : 2u;
+          const int pb = __popc(pmask & ((1u << b) - 1u));
+          const long long cc = (long long)ca * cb;
+          if (!n) {
+            // an empty pair of present levels: q = p_a p_b enters MI, and
+            // S - u u^T is dense there (-u_a u_b)
+            mi0 += mult * (unsigned long long)cc;
+            if (slot) P[pk(kCapL, pa, pb)] = (float)(-cc) * rsqrtf((float)ca * (float)cb) * invT;
+            continue;
+          }
+          const unsigned j = A.lev[b];
+          const int C = (a == b) ? 2 * n : n;
+          a1 += mult * (unsigned)C * (i * j);
+          e2 += mult * (unsigned)C * (unsigned)C;
+          maxc = max(maxc, (unsigned)C);
+          const float fm = (float)mult;
+          hxy += fm * ent_term(C, T);
+          const long long ct = (long long)C * T;
+          if (ct != cc)  // p = p_x p_y exactly contributes nothing
+            mi += fm * __fdividef((float)cc, fT2) * kl_term(__fdividef((float)(ct - cc), (float)cc));
+          if (slot) P[pk(kCapL, pa, pb)] = (float)(ct - cc) * rsqrtf((float)ca * (float)cb) * invT;
+          const unsigned pi = pinfo[t];
+          hkr[pi & 0xFFu] += (uint16_t)(2 * n);
+          hsr[pi >> 8] += (uint16_t)(2 * n);
+          if (dbg_glcm) {
+            int32_t* g = dbg_glcm + (size_t)d * w.ng * w.ng;
+            g[(i - 1) * w.ng + (j - 1)] = C;
+            g[(j - 1) * w.ng + (i - 1)] = C;
+          }
+        }
+      }
+      // difference and sum distributions
+      const float ngf = (float)w.ng;
+      unsigned dk = 0, dk2 = 0, sk = 0, sk2 = 0;
+      float de = 0.f, idm = 0.f, idmn = 0.f, idd = 0.f, idn = 0.f, iv = 0.f, se = 0.f,
+            ce2 = 0.f, ce4 = 0.f;
+      __int128 ce3 = 0;
+      for (int q = 0; q < nk; ++q) {
+        const int c = hkr[q];
+        if (!c) continue;
+        hkr[q] = 0;
+        const int k = kval[q];
+        const float fk = (float)k, fc = (float)c;
+        dk += (unsigned)(k * c);
+        dk2 += (unsigned)(k * k * c);
+        de += ent_term(c, T);
+        idm += __fdividef(fc, 1.f + fk * fk);
+        idmn += __fdividef(fc, 1.f + __fdividef(fk * fk, ngf * ngf));
+        idd += __fdividef(fc, 1.f + fk);
+        idn += __fdividef(fc, 1.f + __fdividef(fk, ngf));
+        if (k) iv += __fdividef(fc, fk * fk);
+      }
+      for (int q = 0; q < ns; ++q) {
+        const int c = hsr[q];
+        if (!c) continue;
+        hsr[q] = 0;
+        const int kk = (int)sval[q] + 2 * w.lev0;
+        sk += (unsigned)(kk * c);
+        sk2 += (unsigned)(kk * kk) * (unsigned)c;
+        se += ent_term(c, T);
+        // T (k - 2 mu): |e| < 2^24 per direction
+        const int e = T * kk - 2 * (int)m1;
+        const float fe = (float)e, fe2 = fe * fe;
+        ce2 += (float)c * fe2;
+        ce4 += (float)c * fe2 * fe2;
+        ce3 += (__int128)((long long)e * e) * ((long long)c * e);
+      }
+      const float MI = (mi + __fdividef((float)mi0, fT2)) * 1.44269504088896341f;  // bits
+      const long long var_num = (long long)T * (long long)m2 - (long long)m1 * m1;
+      fval[0] = __fdividef((float)a1, fT);
+      fval[1] = __fdividef((float)m1, fT);
+      fval[2] = __fdividef(ce4, fT * fT * fT * fT * fT);
+      fval[3] = __fdividef(i128_to_f32(ce3), fT * fT * fT * fT);
+      csn[d] = i128_to_f64(ce3);
+      cst[d] = T;
+      fval[4] = __fdividef(ce2, fT * fT * fT);
+      fval[5] = __fdividef((float)dk2, fT);
+      fval[6] = lane_quot((float)((long long)T * (long long)a1 - (long long)m1 * m1), (float)var_num);
+      fval[7] = __fdividef((float)dk, fT);
+      fval[8] = de;
+      fval[9] = __fdividef((float)((long long)T * (long long)dk2 - (long long)dk * dk), fT2);
+      fval[10] = __fdividef((float)e2, fT2);
+      fval[11] = hxy;
+      fval[12] = lane_quot(-MI, hx);
+      fval[13] = sqrtf(fmaxf(0.f, -expm1f(-2.f * MI)));
+      fval[14] = __fdividef(idm, fT);
+      fval[15] = __fdividef(idmn, fT);
+      fval[16] = __fdividef(idd, fT);
+      fval[17] = __fdividef(idn, fT);
+      fval[18] = __fdividef(iv, fT);
+      fval[19] = __fdividef((float)maxc, fT);
+      fval[20] = __fdividef((float)sk, fT);
+      fval[21] = se;
+      fval[22] = __fdividef((float)var_num, fT2);
+      fval[23] = kNaNf;  // MCC: the deferred solve
+      fval[24] = __fdividef((float)((long long)T * (long long)sk2 - (long long)sk * sk), fT2);
+      fval[25] = __fdividef((float)dk, fT);
+      for (int a = 0; a < m; ++a) mrow[a] = 0;
+    }
+    // the distribution rows of every direction are read: fvd may reuse them
+    __syncwarp((1u << kNumDirs) - 1u);
+#pragma unroll
+    for (int f = 0; f < 26; ++f) row[f] = fval[f];
+  }
+  __syncwarp();
+  // direction means, per feature in direction order (compensated)
+  if (lane < 26) {
+    float s = 0.f, c = 0.f;
+    int n = 0;
+    for (int d = 0; d < kNumDirs; ++d) {
+      const float v = fvd[d * 27 + lane];
+      if (!isnan(v)) {
+        two_sum_add(s, c, v);
+        ++n;
+      }
+    }
+    A.facc[lane] = s;
+    A.fcomp[lane] = c;
+    A.nacc[lane] = n;
+  }
+  __syncwarp();
+  // leave the region zero
+  for (int q = lane; q < 13 * 27; q += 32) fvd[q] = 0.f;
+  for (int q = lane; q < m * S; q += 32) Lsm[q] = (W)0;
+  for (int q = lane; q < 48; q += 32) {
+    pinfo[q] = 0;
+    kval[q] = 0;
+    sval[q] = 0;
+  }
+  __syncwarp();
+}
+
 static __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
                                    int32_t* dbg_glcm, const FbPool* pool) {
   if (A.mc != kMCap) pool = nullptr;
+  if (w.m <= kDirLevels && A.mc == kMCap && job.delta == 1 && job.agg != 1) {
+    if (w.s == 3) return glcm_dir_lanes<3>(w, A, job, dbg_glcm);
+    if (w.s == 5) return glcm_dir_lanes<5>(w, A, job, dbg_glcm);
+    if (w.s == 7) return glcm_dir_lanes<7>(w, A, job, dbg_glcm);
+  }
   if (w.m <= 32 && job.delta == 1 && job.agg != 1) {
     if (w.s == 3) return glcm_family_impl<3>(w, A, job, dbg_glcm, pool);
     if (w.s == 5) return glcm_family_impl<5>(w, A, job, dbg_glcm, pool);
@@ -1563,14 +1871,6 @@ __device__ __forceinline__ float glrlm_feature(int f, const float (&fsr)[7], uns
   if (f == 14) { num = fsr[4]; }
   if (f == 15) { num = fsr[5]; }
   return lane_quot(num, den);
-}
-
-// Compensated (TwoSum) accumulation of one value, and the merge of two such
-// partial sums.
-__device__ __forceinline__ void two_sum_add(float& s, float& c, float v) {
-  const float t = s + v, bv = t - s;
-  c += (s - (t - bv)) + (v - bv);
-  s = t;
 }
 
 // GLRLM (per-direction aggregation) of windows of side S <= 5 with at most

@@ -96,6 +96,17 @@ def test_ct_crop_fbn64_r3_slab_path():
     _check(img, mask, features=ALL, disc_mode=0, bin_count=64, kernel_radius=3)
 
 
+@pytest.mark.parametrize("r", [1, 2])
+def test_ct_crop_glcm_only_fbn64(r):
+    # GLCM alone (no later family clears the big region between voxels):
+    # windows of up to 9 levels take the one-lane-per-direction path, larger
+    # ones the count-matrix path, interleaved in every warp; both must leave
+    # the shared region as they found it
+    img, mask = _crop_ct(seed=9)
+    _check(img, mask, features=list(range(18, 42)) + [96, 97], disc_mode=0, bin_count=64,
+           kernel_radius=r)
+
+
 def test_levels_and_voxel_list_bit_exact():
     import paper_2609_19190_gb300 as fm
     for img, mask, kw in [
