@@ -40,8 +40,8 @@ ALU_LANES_PER_SM = 128  # fp32/int32 lanes per Blackwell SM
 # keyed by the SHA-256 of the CUDA sources it was taken with; a source change
 # makes the figure stale and the bench reports null.
 NCU_TRAFFIC = {
-    # profiles/fr_map_kernel_ct_plain_ncu.md: 24.84 MB read + 68.58 MB written
-    ("ct_plain", "fe534acbef9c3b27d602856d36f1fcbeaaa8bf3c229526b74dc273a509709712"): 93416704,
+    # profiles/fr_map_kernel_ct_plain_ncu.md: 28.07 MB read + 77.60 MB written
+    ("ct_plain", "350f34c1d85ffe2d6e1021a06fdecade42f5384053e68f145f2adea6048d301b"): 105661184,
 }
 
 
