@@ -2519,7 +2519,6 @@ static __device__ void gldm_ngtdm_family(const Win& w, const Arena& A, const FrJ
   const bool do_gldm = (job.families & kFamGLDM) != 0;
   const bool do_ngtdm = (job.families & kFamNGTDM) != 0;
   int* gh = (int*)(A.big + A.L.ghist);  // [mc][28]
-  int* gj = (int*)(A.big + A.L.gj);
   int* ngn = (int*)(A.big + A.L.ngn);
   unsigned long long* ngs = (unsigned long long*)(A.big + A.L.ngs);
   if (w.s == 3 || w.s == 5 || w.s == 7) {
@@ -2587,46 +2586,37 @@ static __device__ void gldm_ngtdm_family(const Win& w, const Arena& A, const FrJ
   if (do_gldm) {
     unsigned si = 0, si2 = 0, sj = 0, sj2 = 0, dnu = 0, dce = 0;  // dce: sum c^2
     float fs[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sde lgl sdl sdh ldl ldh de
-    for (int a0 = 0; a0 < m; a0 += 32) {
-      const int a = a0 + lane;
-      const bool ok = a < m;
-      const unsigned i = ok ? A.lev[a] : 1u;
-      const float fi2 = (float)(i * i), inv_i2 = __fdividef(1.f, fi2);
-      for (int k = 0; k < 27; ++k) {
-        const int c = ok ? gh[a * 28 + k] : 0;
-        const unsigned col = redux_u32((unsigned)c);
-        if (m <= 32)
-          dnu += col * col;
-        else if (lane == 0)
-          gj[k] += (int)col;
-        if (c) {
-          gh[a * 28 + k] = 0;
-          const unsigned J = (unsigned)(k + 1);
-          const float fc = (float)c, fj2 = (float)(J * J), inv_j2 = __fdividef(1.f, fj2);
-          si += (unsigned)c * i;
-          si2 += (unsigned)c * i * i;
-          sj += (unsigned)c * J;
-          sj2 += (unsigned)c * J * J;
-          fs[0] += fc * inv_j2;
-          fs[1] += fc * inv_i2;
-          fs[2] += fc * inv_i2 * inv_j2;
-          fs[3] += fc * fi2 * inv_j2;
-          fs[4] += fc * fj2 * inv_i2;
-          fs[5] += fc * fi2 * fj2;
-          fs[6] += ent_term(c, N);
-          dce += (unsigned)(c * c);
-          if (dbg_gldm) dbg_gldm[(i - 1) * 27 + k] = c;
-        }
-      }
+    // column sums (dependence counts over all levels) first, then one lane
+    // per (level, dependence count) cell
+    if (lane < 27) {
+      unsigned col = 0;
+      for (int a = 0; a < m; ++a) col += (unsigned)gh[a * 28 + lane];
+      dnu = col * col;
     }
-    if (m > 32) {
-      __syncwarp();
-      if (lane < 28) {
-        const unsigned c = (unsigned)gj[lane];
-        gj[lane] = 0;
-        dnu = c * c;
-      }
-      dnu = redux_u32(dnu);
+    dnu = redux_u32(dnu);
+    __syncwarp();
+    for (int t = lane; t < m * 27; t += 32) {
+      const int a = t / 27, k = t - 27 * a;
+      const int c = gh[a * 28 + k];
+      if (!c) continue;
+      gh[a * 28 + k] = 0;
+      const unsigned i = A.lev[a];
+      const float fi2 = (float)(i * i), inv_i2 = __fdividef(1.f, fi2);
+      const unsigned J = (unsigned)(k + 1);
+      const float fc = (float)c, fj2 = (float)(J * J), inv_j2 = __fdividef(1.f, fj2);
+      si += (unsigned)c * i;
+      si2 += (unsigned)c * i * i;
+      sj += (unsigned)c * J;
+      sj2 += (unsigned)c * J * J;
+      fs[0] += fc * inv_j2;
+      fs[1] += fc * inv_i2;
+      fs[2] += fc * inv_i2 * inv_j2;
+      fs[3] += fc * fi2 * inv_j2;
+      fs[4] += fc * fj2 * inv_i2;
+      fs[5] += fc * fi2 * fj2;
+      fs[6] += ent_term(c, N);
+      dce += (unsigned)(c * c);
+      if (dbg_gldm) dbg_gldm[(i - 1) * 27 + k] = c;
     }
     si = redux_u32(si);
     si2 = redux_u32(si2);
