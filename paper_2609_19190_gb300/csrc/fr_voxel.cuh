@@ -1428,90 +1428,150 @@ static __device__ void fb_pool_work(const FbPool& P, const FrMapArgs& args, int 
 // GLCM of windows of side S in {3, 5, 7} with at most kDirLevels levels
 // (distance 1, per-direction aggregation): lane d < 13 takes direction d
 // through every step on its own -- pair counts from the level sets, the
-// entry sums, the difference and sum distributions, the 26 per-direction
-// features and its MCC slot -- so no step needs a warp reduction; the
-// direction means are then taken per feature in direction order.  The
-// distributions are kept per direction over the voxel's distinct gray-level
-// differences and sums (at most one per level pair), numbered once per
-// voxel from bit masks of the values present.
-constexpr int kDirLevels = 9;
-constexpr int kDirPairs = kDirLevels * (kDirLevels + 1) / 2;  // 45
-constexpr int kDirRow = 46;  // u16 per distribution row (23 words: odd stride)
+// entry sums, its MCC slot, the difference and sum distributions and the 26
+// per-direction features -- so no step needs a warp reduction; the direction
+// means are then taken per feature in direction order.  Each lane keeps its
+// pair counts in a row of a shared table; the distributions are read from it
+// in two orders of the level pairs fixed once per voxel (by gray-level
+// difference, by gray-level sum; ties by pair index), so that every class of
+// equal difference (sum) is contiguous and its count is final at its last
+// pair.
+constexpr int kDirLevels = 12;
+constexpr int kDirPairs = kDirLevels * (kDirLevels + 1) / 2;  // 78
+constexpr int kDirRow = kDirPairs;  // u16 per pair-count row (39 words: odd stride)
+constexpr int kDirBytes = 3552;     // bytes of the big region this path uses
+// byte offsets in the big region
+constexpr int kDirMg = 672, kDirW = 1012, kDirOrd = 3040, kDirCnt = 3360;
 
 template <int S>
 __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
                                int32_t* dbg_glcm) {
   using W = typename SliceT<S>::W;
+  static_assert(kDirLevels * S * sizeof(W) <= kDirMg, "level sets");
+  static_assert(kDirMg + 13 * 13 * 2 <= kDirW && kDirW + 13 * kDirRow * 2 <= kDirOrd, "rows");
+  static_assert(13 * 27 * 4 <= kDirOrd - kDirW, "per-direction features over the rows");
   const int lane = lane_id();
   const int m = w.m;
   const int npairs = m * (m + 1) / 2;
   const bool want_mcc = (job.families & kFamMCC) != 0;
-  // layout (this path uses none of the count-matrix path's arrays below
-  // byte 3648, and leaves every byte it uses zero)
-  W* Lsm = (W*)A.big;                                      // [kDirLevels][S]
-  uint16_t* mg = (uint16_t*)(A.big + 512);                 // [13][10] marginals
-  uint16_t* hk = (uint16_t*)(A.big + 776);                 // [13][kDirRow] by difference
-  uint16_t* hs = hk + 13 * kDirRow;                        // [13][kDirRow] by sum
-  uint16_t* pinfo = hs + 13 * kDirRow;                     // [kDirPairs] class ids
-  uint8_t* kval = (uint8_t*)(pinfo + 48);                  // difference of each class
-  uint8_t* sval = kval + 48;                               // sum - 2 lev0 of each class
-  float* fvd = (float*)hk;                                 // [13][27] after the bins
+  W* Lsm = (W*)A.big;                                   // [m][S] level sets
+  uint16_t* mg = (uint16_t*)(A.big + kDirMg);           // [13][13] marginals
+  uint16_t* wt = (uint16_t*)(A.big + kDirW);            // [13][kDirRow] pair counts
+  uint8_t* kord = (uint8_t*)(A.big + kDirOrd);          // pair at each difference position
+  uint8_t* sord = kord + 80;                            // pair at each sum position
+  uint8_t* kpos = sord + 80;                            // difference | 0x80 at a class end
+  uint8_t* spos = kpos + 80;                            // sum - 2 lev0 | 0x80 at a class end
+  uint8_t* cntk = (uint8_t*)(A.big + kDirCnt);          // [64] by difference
+  uint8_t* cnts = cntk + 64;                            // [128] by sum - 2 lev0
+  float* fvd = (float*)(A.big + kDirW);                 // [13][27], after the rows are read
   int* mn = (int*)(A.big + A.L.mn);
   float* mres = (float*)(A.big + A.L.mres);
   float* slots = (float*)(A.big + A.L.slots);
   double* csn = (double*)(A.big + A.L.csn);
   int* cst = (int*)(A.big + A.L.cst);
   acc_reset(A);
+  for (int q = lane; q < 48; q += 32) ((unsigned*)cntk)[q] = 0u;
   W Lm[S], Vm[S];
   slice_masks<S>(w, A, Lm, Vm);
   if (lane < m)
 #pragma unroll
     for (int z = 0; z < S; ++z) Lsm[lane * S + z] = Lm[z];
-  // difference / sum classes of the level pairs: bit masks of the values
-  // present (difference < 64, sum - 2 lev0 < 128), class = rank of the value
-  unsigned km[2] = {0u, 0u}, sm4[4] = {0u, 0u, 0u, 0u};
-  int pk_[2] = {0, 0}, ps_[2] = {0, 0};
+  if (lane < kNumDirs) cst[lane] = 0;
+  __syncwarp();
+  // the two orders of the level pairs: counting sort by value (difference
+  // k <= 63, sum s - 2 lev0 <= 126), ties by pair index
+  int pk_[3], ps_[3];
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
+  for (int r = 0; r < 3; ++r) {
     const int t = 32 * r + lane;
+    pk_[r] = ps_[r] = -1;
     if (t < npairs) {
       int a, b;
       pair_of(t, m, a, b);
-      const int k = (int)A.lev[b] - (int)A.lev[a];
-      const int sm_ = (int)A.lev[a] + (int)A.lev[b] - 2 * w.lev0;
-      pk_[r] = k;
-      ps_[r] = sm_;
-      km[k >> 5] |= 1u << (k & 31);
-      sm4[sm_ >> 5] |= 1u << (sm_ & 31);
+      pk_[r] = (int)A.lev[b] - (int)A.lev[a];
+      ps_[r] = (int)A.lev[a] + (int)A.lev[b] - 2 * w.lev0;
     }
   }
 #pragma unroll
-  for (int q = 0; q < 2; ++q) km[q] = __reduce_or_sync(kFull, km[q]);
+  for (int r = 0; r < 3; ++r) {  // class sizes: the leader of each group adds
+    const bool v = pk_[r] >= 0;
+    const unsigned act = __ballot_sync(kFull, v);
+    if (v) {
+      const unsigned gk = __match_any_sync(act, pk_[r]), gs = __match_any_sync(act, ps_[r]);
+      if ((gk & lanemask_lt()) == 0) cntk[pk_[r]] += (uint8_t)__popc(gk);
+      if ((gs & lanemask_lt()) == 0) cnts[ps_[r]] += (uint8_t)__popc(gs);
+    }
+    __syncwarp();
+  }
+  {  // exclusive prefix sums: class starts (64 differences: 2 per lane;
+     // 128 sums: 4 per lane)
+    const int k0 = cntk[2 * lane], k1 = cntk[2 * lane + 1];
+    const int s0 = cnts[4 * lane], s1 = cnts[4 * lane + 1], s2 = cnts[4 * lane + 2],
+              s3 = cnts[4 * lane + 3];
+    int ik = k0 + k1, is = s0 + s1 + s2 + s3;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) sm4[q] = __reduce_or_sync(kFull, sm4[q]);
-  const int nk = __popc(km[0]) + __popc(km[1]);
-  const int ns = __popc(sm4[0]) + __popc(sm4[1]) + __popc(sm4[2]) + __popc(sm4[3]);
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int t = 32 * r + lane;
-    if (t < npairs) {
-      const int k = pk_[r], sm_ = ps_[r];
-      int kid = __popc(km[0] & ((k >= 32) ? ~0u : ((1u << (k & 31)) - 1u)));
-      if (k >= 32) kid += __popc(km[1] & ((1u << (k & 31)) - 1u));
-      int sid = 0;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int lo = 32 * q;
-        sid += sm_ >= lo + 32 ? __popc(sm4[q])
-                              : sm_ > lo ? __popc(sm4[q] & ((1u << (sm_ - lo)) - 1u)) : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int yk = __shfl_up_sync(kFull, ik, o), ys = __shfl_up_sync(kFull, is, o);
+      if (lane >= o) {
+        ik += yk;
+        is += ys;
       }
-      pinfo[t] = (uint16_t)(kid | (sid << 8));
-      kval[kid] = (uint8_t)k;
-      sval[sid] = (uint8_t)sm_;
     }
+    const int ek = ik - (k0 + k1), es = is - (s0 + s1 + s2 + s3);
+    __syncwarp();
+    cntk[2 * lane] = (uint8_t)ek;
+    cntk[2 * lane + 1] = (uint8_t)(ek + k0);
+    cnts[4 * lane] = (uint8_t)es;
+    cnts[4 * lane + 1] = (uint8_t)(es + s0);
+    cnts[4 * lane + 2] = (uint8_t)(es + s0 + s1);
+    cnts[4 * lane + 3] = (uint8_t)(es + s0 + s1 + s2);
+    __syncwarp();
   }
-  if (lane < kNumDirs) cst[lane] = 0;
-  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {  // positions: class start + rank in pair order
+    const bool v = pk_[r] >= 0;
+    const unsigned act = __ballot_sync(kFull, v);
+    int posk = 0, poss = 0;
+    unsigned gk = 0, gs = 0;
+    if (v) {
+      gk = __match_any_sync(act, pk_[r]);
+      gs = __match_any_sync(act, ps_[r]);
+      posk = cntk[pk_[r]] + __popc(gk & lanemask_lt());
+      poss = cnts[ps_[r]] + __popc(gs & lanemask_lt());
+      kord[posk] = (uint8_t)(32 * r + lane);
+      kpos[posk] = (uint8_t)pk_[r];
+      sord[poss] = (uint8_t)(32 * r + lane);
+      spos[poss] = (uint8_t)ps_[r];
+    }
+    __syncwarp();
+    if (v) {
+      if ((gk & lanemask_lt()) == 0) cntk[pk_[r]] += (uint8_t)__popc(gk);
+      if ((gs & lanemask_lt()) == 0) cnts[ps_[r]] += (uint8_t)__popc(gs);
+    }
+    __syncwarp();
+  }
+  {  // mark the last position of every class
+    int fk[3], fs[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int p = 32 * r + lane;
+      fk[r] = fs[r] = 0;
+      if (p < npairs) {
+        fk[r] = (p == npairs - 1 || kpos[p + 1] != kpos[p]) ? 0x80 : 0;
+        fs[r] = (p == npairs - 1 || spos[p + 1] != spos[p]) ? 0x80 : 0;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int p = 32 * r + lane;
+      if (p < npairs) {
+        kpos[p] |= (uint8_t)fk[r];
+        spos[p] |= (uint8_t)fs[r];
+      }
+    }
+    __syncwarp();
+  }
   if (lane < kNumDirs) {
     const int d = lane;
     int dz, dy, dx;
@@ -1524,7 +1584,6 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
 #pragma unroll
     for (int z = 0; z < S; ++z) npz += (unsigned)popc_w<W>(Vm[z] & fV[z]);
     const int T = 2 * (int)npz;
-    float* row = fvd + d * 27;  // written after the distributions are read
     float fval[26];
     if (T == 0) {
       mn[d] = 0;
@@ -1533,7 +1592,8 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
       for (int f = 0; f < 26; ++f) fval[f] = kNaNf;
     } else {
       const float fT = (float)T, fT2 = fT * fT, invT = __fdividef(1.f, fT);
-      uint16_t* mrow = mg + d * 10;
+      uint16_t* mrow = mg + d * 13;
+      uint16_t* wrow = wt + d * kDirRow;
       // marginals c_a = |L_a & fwd(V)| + |L_a & bwd(V)|
       unsigned m1 = 0, m2 = 0, pmask = 0;
       float hx = 0.f;
@@ -1560,8 +1620,6 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
         for (int t = 0; t < kSlot; ++t) P[t] = 0.f;
       mn[d] = slot ? present : 0;
       if (!slot) mres[d] = kNaNf;
-      uint16_t* hkr = hk + d * kDirRow;
-      uint16_t* hsr = hs + d * kDirRow;
       unsigned a1 = 0, e2 = 0, maxc = 0;
       unsigned long long mi0 = 0;
       float hxy = 0.f, mi = 0.f;
@@ -1587,6 +1645,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
               n += popc_w<W>(lb & fa[z]) + popc_w<W>(lb & ba[z]);
             }
           }
+          wrow[t] = (uint16_t)(2 * n);  // the pair's weight in both distributions
           const int cb = mrow[b];
           if (!ca || !cb) continue;
           const unsigned mult = (a == b) ? 1u : 2u;
@@ -1610,9 +1669,6 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
           if (ct != cc)  // p = p_x p_y exactly contributes nothing
             mi += fm * __fdividef((float)cc, fT2) * kl_term(__fdividef((float)(ct - cc), (float)cc));
           if (slot) P[pk(kCapL, pa, pb)] = (float)(ct - cc) * rsqrtf((float)ca * (float)cb) * invT;
-          const unsigned pi = pinfo[t];
-          hkr[pi & 0xFFu] += (uint16_t)(2 * n);
-          hsr[pi >> 8] += (uint16_t)(2 * n);
           if (dbg_glcm) {
             int32_t* g = dbg_glcm + (size_t)d * w.ng * w.ng;
             g[(i - 1) * w.ng + (j - 1)] = C;
@@ -1620,17 +1676,22 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
           }
         }
       }
-      // difference and sum distributions
+      // difference distribution: pairs in difference order, a class's count
+      // is complete at its last pair
       const float ngf = (float)w.ng;
       unsigned dk = 0, dk2 = 0, sk = 0, sk2 = 0;
       float de = 0.f, idm = 0.f, idmn = 0.f, idd = 0.f, idn = 0.f, iv = 0.f, se = 0.f,
             ce2 = 0.f, ce4 = 0.f;
       __int128 ce3 = 0;
-      for (int q = 0; q < nk; ++q) {
-        const int c = hkr[q];
+      int acc = 0;
+      for (int p = 0; p < npairs; ++p) {
+        const int v = kpos[p];
+        acc += wrow[kord[p]];
+        if (!(v & 0x80)) continue;
+        const int c = acc;
+        acc = 0;
         if (!c) continue;
-        hkr[q] = 0;
-        const int k = kval[q];
+        const int k = v & 0x7F;
         const float fk = (float)k, fc = (float)c;
         dk += (unsigned)(k * c);
         dk2 += (unsigned)(k * k * c);
@@ -1641,11 +1702,15 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
         idn += __fdividef(fc, 1.f + __fdividef(fk, ngf));
         if (k) iv += __fdividef(fc, fk * fk);
       }
-      for (int q = 0; q < ns; ++q) {
-        const int c = hsr[q];
+      // sum distribution, the same way
+      for (int p = 0; p < npairs; ++p) {
+        const int v = spos[p];
+        acc += wrow[sord[p]];
+        if (!(v & 0x80)) continue;
+        const int c = acc;
+        acc = 0;
         if (!c) continue;
-        hsr[q] = 0;
-        const int kk = (int)sval[q] + 2 * w.lev0;
+        const int kk = (v & 0x7F) + 2 * w.lev0;
         sk += (unsigned)(kk * c);
         sk2 += (unsigned)(kk * kk) * (unsigned)c;
         se += ent_term(c, T);
@@ -1686,10 +1751,10 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
       fval[23] = kNaNf;  // MCC: the deferred solve
       fval[24] = __fdividef((float)((long long)T * (long long)sk2 - (long long)sk * sk), fT2);
       fval[25] = __fdividef((float)dk, fT);
-      for (int a = 0; a < m; ++a) mrow[a] = 0;
     }
-    // the distribution rows of every direction are read: fvd may reuse them
+    // every direction's rows are read: the features may reuse them
     __syncwarp((1u << kNumDirs) - 1u);
+    float* row = fvd + d * 27;
 #pragma unroll
     for (int f = 0; f < 26; ++f) row[f] = fval[f];
   }
@@ -1710,21 +1775,17 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
     A.nacc[lane] = n;
   }
   __syncwarp();
-  // leave the region zero
-  for (int q = lane; q < 13 * 27; q += 32) fvd[q] = 0.f;
-  for (int q = lane; q < m * S; q += 32) Lsm[q] = (W)0;
-  for (int q = lane; q < 48; q += 32) {
-    pinfo[q] = 0;
-    kval[q] = 0;
-    sval[q] = 0;
-  }
+  // leave the region zero (the count-matrix path and the later families
+  // expect it so)
+  for (int q = lane; q < kDirBytes / 16; q += 32) ((uint4*)A.big)[q] = make_uint4(0u, 0u, 0u, 0u);
   __syncwarp();
 }
 
 static __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
                                    int32_t* dbg_glcm, const FbPool* pool) {
   if (A.mc != kMCap) pool = nullptr;
-  if (w.m <= kDirLevels && A.mc == kMCap && job.delta == 1 && job.agg != 1) {
+  if (w.m <= kDirLevels && A.mc == kMCap && A.L.mn >= kDirBytes && job.delta == 1 &&
+      job.agg != 1) {
     if (w.s == 3) return glcm_dir_lanes<3>(w, A, job, dbg_glcm);
     if (w.s == 5) return glcm_dir_lanes<5>(w, A, job, dbg_glcm);
     if (w.s == 7) return glcm_dir_lanes<7>(w, A, job, dbg_glcm);
