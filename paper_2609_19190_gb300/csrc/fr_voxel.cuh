@@ -1572,8 +1572,13 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
     }
     __syncwarp();
   }
-  if (lane < kNumDirs) {
-    const int d = lane;
+  // lanes d and d + 16 share direction d: both take the marginals; lane h
+  // takes the pair rows a = h, h + 2, ..., their sums meet by one exchange;
+  // lane 0 of the pair reads the difference order, lane 1 the sum order
+  const int d = lane & 15, h = lane >> 4;
+  const unsigned pm = (1u << d) | (1u << (d + 16));
+  constexpr unsigned kPairLanes = ((1u << kNumDirs) - 1u) * 0x10001u;
+  if (d < kNumDirs) {
     int dz, dy, dx;
     dir_of(d, dz, dy, dx);
     const SliceDir<S> D(dz, dy, dx);
@@ -1585,16 +1590,18 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
     for (int z = 0; z < S; ++z) npz += (unsigned)popc_w<W>(Vm[z] & fV[z]);
     const int T = 2 * (int)npz;
     float fval[26];
-    if (T == 0) {
-      mn[d] = 0;
-      mres[d] = kNaNf;
 #pragma unroll
-      for (int f = 0; f < 26; ++f) fval[f] = kNaNf;
+    for (int f = 0; f < 26; ++f) fval[f] = kNaNf;
+    if (T == 0) {
+      if (!h) {
+        mn[d] = 0;
+        mres[d] = kNaNf;
+      }
     } else {
       const float fT = (float)T, fT2 = fT * fT, invT = __fdividef(1.f, fT);
       uint16_t* mrow = mg + d * 13;
       uint16_t* wrow = wt + d * kDirRow;
-      // marginals c_a = |L_a & fwd(V)| + |L_a & bwd(V)|
+      // marginals c_a = |L_a & fwd(V)| + |L_a & bwd(V)| (both lanes)
       unsigned m1 = 0, m2 = 0, pmask = 0;
       float hx = 0.f;
       for (int a = 0; a < m; ++a) {
@@ -1604,7 +1611,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
           const W la = Lsm[a * S + z];
           c += (unsigned)(popc_w<W>(la & fV[z]) + popc_w<W>(la & bV[z]));
         }
-        mrow[a] = (uint16_t)c;
+        if (!h) mrow[a] = (uint16_t)c;
         if (c) {
           const unsigned i = A.lev[a];
           m1 += i * c;
@@ -1617,14 +1624,16 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
       const bool slot = want_mcc && present >= 2;
       float* P = slots + d * kSlot;
       if (slot)
-        for (int t = 0; t < kSlot; ++t) P[t] = 0.f;
-      mn[d] = slot ? present : 0;
-      if (!slot) mres[d] = kNaNf;
+        for (int t = h; t < kSlot; t += 2) P[t] = 0.f;
+      if (!h) {
+        mn[d] = slot ? present : 0;
+        if (!slot) mres[d] = kNaNf;
+      }
+      __syncwarp(pm);
       unsigned a1 = 0, e2 = 0, maxc = 0;
       unsigned long long mi0 = 0;
       float hxy = 0.f, mi = 0.f;
-      int t = 0;
-      for (int a = 0; a < m; ++a) {
+      for (int a = h; a < m; a += 2) {
         W la[S], fa[S], ba[S];
 #pragma unroll
         for (int z = 0; z < S; ++z) la[z] = Lsm[a * S + z];
@@ -1633,6 +1642,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
         const int ca = mrow[a];
         const unsigned i = A.lev[a];
         const int pa = __popc(pmask & ((1u << a) - 1u));
+        int t = a * m - ((a * (a - 1)) >> 1);  // pair (a, a)
         for (int b = a; b < m; ++b, ++t) {
           int n = 0;
           if (b == a) {
@@ -1676,87 +1686,103 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
           }
         }
       }
-      // difference distribution: pairs in difference order, a class's count
-      // is complete at its last pair
-      const float ngf = (float)w.ng;
-      unsigned dk = 0, dk2 = 0, sk = 0, sk2 = 0;
-      float de = 0.f, idm = 0.f, idmn = 0.f, idd = 0.f, idn = 0.f, iv = 0.f, se = 0.f,
-            ce2 = 0.f, ce4 = 0.f;
-      __int128 ce3 = 0;
-      int acc = 0;
-      for (int p = 0; p < npairs; ++p) {
-        const int v = kpos[p];
-        acc += wrow[kord[p]];
-        if (!(v & 0x80)) continue;
-        const int c = acc;
-        acc = 0;
-        if (!c) continue;
-        const int k = v & 0x7F;
-        const float fk = (float)k, fc = (float)c;
-        dk += (unsigned)(k * c);
-        dk2 += (unsigned)(k * k * c);
-        de += ent_term(c, T);
-        idm += __fdividef(fc, 1.f + fk * fk);
-        idmn += __fdividef(fc, 1.f + __fdividef(fk * fk, ngf * ngf));
-        idd += __fdividef(fc, 1.f + fk);
-        idn += __fdividef(fc, 1.f + __fdividef(fk, ngf));
-        if (k) iv += __fdividef(fc, fk * fk);
+      // the two halves' sums (a + b == b + a: both lanes get the same value)
+      a1 += __shfl_xor_sync(pm, a1, 16);
+      e2 += __shfl_xor_sync(pm, e2, 16);
+      maxc = max(maxc, __shfl_xor_sync(pm, maxc, 16));
+      mi0 += __shfl_xor_sync(pm, mi0, 16);
+      hxy += __shfl_xor_sync(pm, hxy, 16);
+      mi += __shfl_xor_sync(pm, mi, 16);
+      __syncwarp(pm);  // the row is complete
+      if (!h) {
+        // difference distribution: pairs in difference order, a class's
+        // count is complete at its last pair
+        const float ngf = (float)w.ng;
+        unsigned dk = 0, dk2 = 0;
+        float de = 0.f, idm = 0.f, idmn = 0.f, idd = 0.f, idn = 0.f, iv = 0.f;
+        int acc = 0;
+        for (int p = 0; p < npairs; ++p) {
+          const int v = kpos[p];
+          acc += wrow[kord[p]];
+          if (!(v & 0x80)) continue;
+          const int c = acc;
+          acc = 0;
+          if (!c) continue;
+          const int k = v & 0x7F;
+          const float fk = (float)k, fc = (float)c;
+          dk += (unsigned)(k * c);
+          dk2 += (unsigned)(k * k * c);
+          de += ent_term(c, T);
+          idm += __fdividef(fc, 1.f + fk * fk);
+          idmn += __fdividef(fc, 1.f + __fdividef(fk * fk, ngf * ngf));
+          idd += __fdividef(fc, 1.f + fk);
+          idn += __fdividef(fc, 1.f + __fdividef(fk, ngf));
+          if (k) iv += __fdividef(fc, fk * fk);
+        }
+        const float MI = (mi + __fdividef((float)mi0, fT2)) * 1.44269504088896341f;  // bits
+        const long long var_num = (long long)T * (long long)m2 - (long long)m1 * m1;
+        fval[0] = __fdividef((float)a1, fT);
+        fval[1] = __fdividef((float)m1, fT);
+        fval[5] = __fdividef((float)dk2, fT);
+        fval[6] = lane_quot((float)((long long)T * (long long)a1 - (long long)m1 * m1),
+                            (float)var_num);
+        fval[7] = __fdividef((float)dk, fT);
+        fval[8] = de;
+        fval[9] = __fdividef((float)((long long)T * (long long)dk2 - (long long)dk * dk), fT2);
+        fval[10] = __fdividef((float)e2, fT2);
+        fval[11] = hxy;
+        fval[12] = lane_quot(-MI, hx);
+        fval[13] = sqrtf(fmaxf(0.f, -expm1f(-2.f * MI)));
+        fval[14] = __fdividef(idm, fT);
+        fval[15] = __fdividef(idmn, fT);
+        fval[16] = __fdividef(idd, fT);
+        fval[17] = __fdividef(idn, fT);
+        fval[18] = __fdividef(iv, fT);
+        fval[19] = __fdividef((float)maxc, fT);
+        fval[22] = __fdividef((float)var_num, fT2);
+        fval[25] = __fdividef((float)dk, fT);
+      } else {
+        // sum distribution, the same way
+        unsigned sk = 0, sk2 = 0;
+        float se = 0.f, ce2 = 0.f, ce4 = 0.f;
+        __int128 ce3 = 0;
+        int acc = 0;
+        for (int p = 0; p < npairs; ++p) {
+          const int v = spos[p];
+          acc += wrow[sord[p]];
+          if (!(v & 0x80)) continue;
+          const int c = acc;
+          acc = 0;
+          if (!c) continue;
+          const int kk = (v & 0x7F) + 2 * w.lev0;
+          sk += (unsigned)(kk * c);
+          sk2 += (unsigned)(kk * kk) * (unsigned)c;
+          se += ent_term(c, T);
+          // T (k - 2 mu): |e| < 2^24 per direction
+          const int e = T * kk - 2 * (int)m1;
+          const float fe = (float)e, fe2 = fe * fe;
+          ce2 += (float)c * fe2;
+          ce4 += (float)c * fe2 * fe2;
+          ce3 += (__int128)((long long)e * e) * ((long long)c * e);
+        }
+        fval[2] = __fdividef(ce4, fT * fT * fT * fT * fT);
+        fval[3] = __fdividef(i128_to_f32(ce3), fT * fT * fT * fT);
+        csn[d] = i128_to_f64(ce3);
+        cst[d] = T;
+        fval[4] = __fdividef(ce2, fT * fT * fT);
+        fval[20] = __fdividef((float)sk, fT);
+        fval[21] = se;
+        fval[24] = __fdividef((float)((long long)T * (long long)sk2 - (long long)sk * sk), fT2);
       }
-      // sum distribution, the same way
-      for (int p = 0; p < npairs; ++p) {
-        const int v = spos[p];
-        acc += wrow[sord[p]];
-        if (!(v & 0x80)) continue;
-        const int c = acc;
-        acc = 0;
-        if (!c) continue;
-        const int kk = (v & 0x7F) + 2 * w.lev0;
-        sk += (unsigned)(kk * c);
-        sk2 += (unsigned)(kk * kk) * (unsigned)c;
-        se += ent_term(c, T);
-        // T (k - 2 mu): |e| < 2^24 per direction
-        const int e = T * kk - 2 * (int)m1;
-        const float fe = (float)e, fe2 = fe * fe;
-        ce2 += (float)c * fe2;
-        ce4 += (float)c * fe2 * fe2;
-        ce3 += (__int128)((long long)e * e) * ((long long)c * e);
-      }
-      const float MI = (mi + __fdividef((float)mi0, fT2)) * 1.44269504088896341f;  // bits
-      const long long var_num = (long long)T * (long long)m2 - (long long)m1 * m1;
-      fval[0] = __fdividef((float)a1, fT);
-      fval[1] = __fdividef((float)m1, fT);
-      fval[2] = __fdividef(ce4, fT * fT * fT * fT * fT);
-      fval[3] = __fdividef(i128_to_f32(ce3), fT * fT * fT * fT);
-      csn[d] = i128_to_f64(ce3);
-      cst[d] = T;
-      fval[4] = __fdividef(ce2, fT * fT * fT);
-      fval[5] = __fdividef((float)dk2, fT);
-      fval[6] = lane_quot((float)((long long)T * (long long)a1 - (long long)m1 * m1), (float)var_num);
-      fval[7] = __fdividef((float)dk, fT);
-      fval[8] = de;
-      fval[9] = __fdividef((float)((long long)T * (long long)dk2 - (long long)dk * dk), fT2);
-      fval[10] = __fdividef((float)e2, fT2);
-      fval[11] = hxy;
-      fval[12] = lane_quot(-MI, hx);
-      fval[13] = sqrtf(fmaxf(0.f, -expm1f(-2.f * MI)));
-      fval[14] = __fdividef(idm, fT);
-      fval[15] = __fdividef(idmn, fT);
-      fval[16] = __fdividef(idd, fT);
-      fval[17] = __fdividef(idn, fT);
-      fval[18] = __fdividef(iv, fT);
-      fval[19] = __fdividef((float)maxc, fT);
-      fval[20] = __fdividef((float)sk, fT);
-      fval[21] = se;
-      fval[22] = __fdividef((float)var_num, fT2);
-      fval[23] = kNaNf;  // MCC: the deferred solve
-      fval[24] = __fdividef((float)((long long)T * (long long)sk2 - (long long)sk * sk), fT2);
-      fval[25] = __fdividef((float)dk, fT);
     }
-    // every direction's rows are read: the features may reuse them
-    __syncwarp((1u << kNumDirs) - 1u);
+    // every direction's rows are read: the features may reuse them; each
+    // lane of a pair writes its own features (fval[23], MCC, stays NaN)
+    __syncwarp(kPairLanes);
     float* row = fvd + d * 27;
+    const unsigned mine = h ? 0x0130001Cu : 0x02CFFFE3u;  // bit f: this lane's feature f
 #pragma unroll
-    for (int f = 0; f < 26; ++f) row[f] = fval[f];
+    for (int f = 0; f < 26; ++f)
+      if ((mine >> f) & 1u) row[f] = fval[f];
   }
   __syncwarp();
   // direction means, per feature in direction order (compensated)
