@@ -2090,10 +2090,193 @@ __device__ void glrlm_masks_packed(const Win& w, const Arena& A, int32_t* dbg_gl
   __syncwarp();
 }
 
+// GLRLM of windows of side S <= 5 with at most 16 levels (per-direction
+// aggregation): lanes d and d + 16 take direction d.  The set E_d of VOI
+// voxels whose successor u + d has the same level is built once per direction
+// (the union over levels of L_a & fwd(L_a)); run starts are V minus bwd(E_d),
+// and R_j = E_d & fwd(R_{j-1}) marks the voxels that begin a chain of j + 1
+// equal levels, for every level at once.  Each lane of the pair then counts
+// the runs of its levels (a = h, h + 2, ...) as |L_a & starts & R_j|, keeps
+// their per-cell terms, and the pair's sums meet by one exchange each; the
+// direction means follow per feature in direction order.
+constexpr int kRunLevels = 16;
+// byte offsets in the shared-memory big region (everything below byte 2512 is
+// cleared on exit; the run-count cells from byte 3264 lie in bytes that no
+// family needs zero: GLCM's solver scratch and MCC slots, written before use)
+constexpr int kRunR = 320, kRunS0 = 1360, kRunF = 1620, kRunClear = 2512, kRunCells = 3264;
+
+template <int S>
+__device__ void glrlm_dir_lanes(const Win& w, const Arena& A, int32_t* dbg_glrlm) {
+  using W = typename SliceT<S>::W;
+  static_assert(sizeof(W) == 4 && kRunLevels * S * 4 <= kRunR, "level sets");
+  static_assert(kRunR + 13 * (S - 1) * S * 4 <= kRunS0 && kRunS0 + 13 * S * 4 <= kRunF, "sets");
+  static_assert(kRunF + 13 * 17 * 4 <= kRunClear, "feature rows");
+  static_assert(kRunCells + 32 * 8 * S * 2 <= 8000, "run-count cells");
+  const int lane = lane_id();
+  const int m = w.m;
+  W* Lsm = (W*)A.big;                              // [m][S]
+  W* Rsm = (W*)(A.big + kRunR);                    // [13][S - 1][S]: R_1 .. R_{S-1}
+  W* S0sm = (W*)(A.big + kRunS0);                  // [13][S] run starts
+  float* fvd = (float*)(A.big + kRunF);            // [13][17] features
+  uint16_t* cells = (uint16_t*)(A.big + kRunCells);  // [32 lanes][8][S] run counts
+  W Lm[S], Vm[S];
+  slice_masks<S>(w, A, Lm, Vm);
+  if (lane < m)
+#pragma unroll
+    for (int z = 0; z < S; ++z) Lsm[lane * S + z] = Lm[z];
+  __syncwarp();
+  const int d = lane & 15, h = lane >> 4;
+  const unsigned pm = (1u << d) | (1u << (d + 16));
+  if (d < kNumDirs) {
+    int dz, dy, dx;
+    dir_of(d, dz, dy, dx);
+    const SliceDir<S> D(dz, dy, dx);
+    // E_d over this lane's levels, then the pair's union
+    W E[S];
+#pragma unroll
+    for (int z = 0; z < S; ++z) E[z] = 0;
+    for (int a = h; a < m; a += 2) {
+      W la[S], fa[S];
+#pragma unroll
+      for (int z = 0; z < S; ++z) la[z] = Lsm[a * S + z];
+      D.fwd(la, fa);
+#pragma unroll
+      for (int z = 0; z < S; ++z) E[z] |= la[z] & fa[z];
+    }
+#pragma unroll
+    for (int z = 0; z < S; ++z) E[z] |= __shfl_xor_sync(pm, E[z], 16);
+    W* Rd = Rsm + d * (S - 1) * S;
+    W* S0 = S0sm + d * S;
+    if (!h) {
+      W T[S], R[S];
+      D.bwd(E, T);
+#pragma unroll
+      for (int z = 0; z < S; ++z) {
+        S0[z] = Vm[z] & ~T[z];
+        R[z] = E[z];
+      }
+#pragma unroll
+      for (int j = 1; j < S; ++j) {
+#pragma unroll
+        for (int z = 0; z < S; ++z) Rd[(j - 1) * S + z] = R[z];
+        if (j + 1 < S) {
+          D.fwd(R, T);
+#pragma unroll
+          for (int z = 0; z < S; ++z) R[z] = E[z] & T[z];
+        }
+      }
+    }
+    __syncwarp(pm);
+    // runs of this lane's levels: c_j = |L_a & starts & R_j|, runs of length
+    // exactly j + 1 = c_j - c_{j+1}
+    uint16_t* mycells = cells + lane * 8 * S;
+    unsigned nr = 0, sj = 0, sj2 = 0, glnu = 0, si = 0, si2 = 0;
+    unsigned col[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) col[j] = 0;
+    float fs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sre lgl srl srh lrl lrh
+    int q = 0;
+    for (int a = h; a < m; a += 2, ++q) {
+      W base[S];
+      unsigned c[S + 1];
+      c[0] = 0;
+#pragma unroll
+      for (int z = 0; z < S; ++z) {
+        base[z] = Lsm[a * S + z] & S0[z];
+        c[0] += (unsigned)popc_w<W>(base[z]);
+      }
+#pragma unroll
+      for (int j = 1; j < S; ++j) {
+        c[j] = 0;
+#pragma unroll
+        for (int z = 0; z < S; ++z) c[j] += (unsigned)popc_w<W>(base[z] & Rd[(j - 1) * S + z]);
+      }
+      c[S] = 0;
+      const unsigned i = A.lev[a];
+      const float fi2 = (float)(i * i), inv_i2 = __fdividef(1.f, fi2);
+      unsigned row = 0;
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const unsigned cnt = c[j] - c[j + 1];
+        mycells[q * S + j] = (uint16_t)cnt;
+        const unsigned J = (unsigned)(j + 1);
+        const float fc = (float)cnt, fj2 = (float)(J * J), inv_j2 = 1.f / (float)(J * J);
+        row += cnt;
+        col[j] += cnt;
+        sj += cnt * J;
+        sj2 += cnt * J * J;
+        fs[0] += fc * inv_j2;
+        fs[1] += fc * inv_i2;
+        fs[2] += fc * inv_i2 * inv_j2;
+        fs[3] += fc * fi2 * inv_j2;
+        fs[4] += fc * fj2 * inv_i2;
+        fs[5] += fc * fi2 * fj2;
+        if (dbg_glrlm && cnt) dbg_glrlm[((size_t)d * w.ng + (i - 1)) * w.s + j] = (int)cnt;
+      }
+      nr += row;
+      glnu += row * row;
+      si += row * i;
+      si2 += row * i * i;
+    }
+    // the pair's totals (integer sums, and a + b == b + a for the floats)
+    nr += __shfl_xor_sync(pm, nr, 16);
+    sj += __shfl_xor_sync(pm, sj, 16);
+    sj2 += __shfl_xor_sync(pm, sj2, 16);
+    glnu += __shfl_xor_sync(pm, glnu, 16);
+    si += __shfl_xor_sync(pm, si, 16);
+    si2 += __shfl_xor_sync(pm, si2, 16);
+    unsigned rlnu = 0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const unsigned cj = col[j] + __shfl_xor_sync(pm, col[j], 16);
+      rlnu += cj * cj;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) fs[k] += __shfl_xor_sync(pm, fs[k], 16);
+    float ent = 0.f;
+    for (int qq = 0; qq < q; ++qq)
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const int cnt = mycells[qq * S + j];
+        if (cnt) ent += ent_term(cnt, (int)nr);
+      }
+    ent += __shfl_xor_sync(pm, ent, 16);
+    const float fsr[7] = {fs[0], fs[1], fs[2], fs[3], fs[4], fs[5], ent};
+    const float nvf = (float)w.nv;
+    float* row = fvd + d * 17;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int f = 8 * h + k;
+      row[f] = glrlm_feature(f, fsr, nr, sj2, glnu, rlnu, si, si2, sj, nvf);
+    }
+  }
+  __syncwarp();
+  // direction means, per feature in direction order (compensated)
+  if (lane < 16) {
+    float s = 0.f, c = 0.f;
+    int n = 0;
+    for (int dd = 0; dd < kNumDirs; ++dd) {
+      const float v = fvd[dd * 17 + lane];
+      if (!isnan(v)) {
+        two_sum_add(s, c, v);
+        ++n;
+      }
+    }
+    A.fv[42 + lane] = n ? __fdividef(s + c, (float)n) : kNaNf;
+  }
+  __syncwarp();
+  for (int t = lane; t < kRunClear / 16; t += 32) ((uint4*)A.big)[t] = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp();
+}
+
 // merged: the 13 directions' runs go into one matrix, whose features are
 // taken once (RunPercentage over 13 N_v: each voxel lies on one run per
 // direction).
 static __device__ void glrlm_family(const Win& w, const Arena& A, bool merged, int32_t* dbg_glrlm) {
+  if (!merged && w.m <= kRunLevels && A.mc == kMCap) {
+    if (w.s == 3) return glrlm_dir_lanes<3>(w, A, dbg_glrlm);
+    if (w.s == 5) return glrlm_dir_lanes<5>(w, A, dbg_glrlm);
+  }
   if (!merged && w.m <= 16) {
     if (w.s == 3) return glrlm_masks_packed<3>(w, A, dbg_glrlm);
     if (w.s == 5) return glrlm_masks_packed<5>(w, A, dbg_glrlm);
