@@ -1425,7 +1425,7 @@ static __device__ void fb_pool_work(const FbPool& P, const FrMapArgs& args, int 
 
 // pool: many-level MCC solves go to the CTA pool (windows in shared memory);
 // null solves them inline.  The caller runs glcm_finish after the pool.
-// GLCM of windows of side S in {3, 5, 7} with at most kDirLevels levels
+// GLCM of windows of side S in {3, 5, 7} with at most DirLayout<S>::kLv levels
 // (distance 1, per-direction aggregation): lane d < 13 takes direction d
 // through every step on its own -- pair counts from the level sets, the
 // entry sums, its MCC slot, the difference and sum distributions and the 26
@@ -1436,34 +1436,51 @@ static __device__ void fb_pool_work(const FbPool& P, const FrMapArgs& args, int 
 // difference, by gray-level sum; ties by pair index), so that every class of
 // equal difference (sum) is contiguous and its count is final at its last
 // pair.
-constexpr int kDirLevels = 12;
-constexpr int kDirPairs = kDirLevels * (kDirLevels + 1) / 2;  // 78
-constexpr int kDirRow = kDirPairs;  // u16 per pair-count row (39 words: odd stride)
-constexpr int kDirBytes = 3552;     // bytes of the big region this path uses
-// byte offsets in the big region
-constexpr int kDirMg = 672, kDirW = 1012, kDirOrd = 3040, kDirCnt = 3360;
+// Layout of the path in the shared-memory big region, per window side:
+// side 3 and 5 take up to 16 levels with byte pair counts (a direction of a
+// side-5 window has at most 100 voxel pairs, so a count 2n <= 200), side 7 up
+// to 12 levels with 16-bit counts.  Rows have an odd number of words.
+template <int S>
+struct DirLayout {
+  static constexpr int kLv = S <= 5 ? 16 : 12;
+  static constexpr int kPairs = kLv * (kLv + 1) / 2;  // 136 or 78
+  using Cnt = typename std::conditional<(S <= 5), uint8_t, uint16_t>::type;
+  static constexpr int kRow = S <= 5 ? 140 : 78;      // counts per row
+  static constexpr int kMgRow = kLv + 1;              // marginals per row
+  static constexpr int kMg = S <= 5 ? 320 : 672;      // byte offsets
+  static constexpr int kW = S <= 5 ? 764 : 1012;
+  static constexpr int kOrd = kW + 13 * kRow * (int)sizeof(Cnt);
+  static constexpr int kOrdLen = (kPairs + 3) & ~3;
+  static constexpr int kCnt = kOrd + 4 * kOrdLen;
+  static constexpr int kBytes = (kCnt + 192 + 15) / 16 * 16;
+};
 
 template <int S>
 __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
-                               int32_t* dbg_glcm) {
+                               int32_t* dbg_glcm, const FbPool* pool) {
   using W = typename SliceT<S>::W;
-  static_assert(kDirLevels * S * sizeof(W) <= kDirMg, "level sets");
-  static_assert(kDirMg + 13 * 13 * 2 <= kDirW && kDirW + 13 * kDirRow * 2 <= kDirOrd, "rows");
-  static_assert(13 * 27 * 4 <= kDirOrd - kDirW, "per-direction features over the rows");
+  using Lay = DirLayout<S>;
+  using Cnt = typename Lay::Cnt;
+  constexpr int kRounds = (Lay::kPairs + 31) / 32;
+  static_assert(Lay::kLv * S * sizeof(W) <= Lay::kMg, "level sets");
+  static_assert(Lay::kMg + 13 * Lay::kMgRow * 2 <= Lay::kW, "marginals");
+  static_assert(13 * 27 * 4 <= Lay::kOrd - Lay::kW, "per-direction features over the rows");
+  static_assert(Lay::kBytes <= 3648, "below the MCC bookkeeping");
+  static_assert(S > 5 || 2 * S * S * (S - 1) < 256, "byte counts");
   const int lane = lane_id();
   const int m = w.m;
   const int npairs = m * (m + 1) / 2;
   const bool want_mcc = (job.families & kFamMCC) != 0;
   W* Lsm = (W*)A.big;                                   // [m][S] level sets
-  uint16_t* mg = (uint16_t*)(A.big + kDirMg);           // [13][13] marginals
-  uint16_t* wt = (uint16_t*)(A.big + kDirW);            // [13][kDirRow] pair counts
-  uint8_t* kord = (uint8_t*)(A.big + kDirOrd);          // pair at each difference position
-  uint8_t* sord = kord + 80;                            // pair at each sum position
-  uint8_t* kpos = sord + 80;                            // difference | 0x80 at a class end
-  uint8_t* spos = kpos + 80;                            // sum - 2 lev0 | 0x80 at a class end
-  uint8_t* cntk = (uint8_t*)(A.big + kDirCnt);          // [64] by difference
+  uint16_t* mg = (uint16_t*)(A.big + Lay::kMg);         // [13][kMgRow] marginals
+  Cnt* wt = (Cnt*)(A.big + Lay::kW);                    // [13][kRow] pair counts
+  uint8_t* kord = (uint8_t*)(A.big + Lay::kOrd);        // pair at each difference position
+  uint8_t* sord = kord + Lay::kOrdLen;                  // pair at each sum position
+  uint8_t* kpos = sord + Lay::kOrdLen;                  // difference | 0x80 at a class end
+  uint8_t* spos = kpos + Lay::kOrdLen;                  // sum - 2 lev0 | 0x80 at a class end
+  uint8_t* cntk = (uint8_t*)(A.big + Lay::kCnt);        // [64] by difference
   uint8_t* cnts = cntk + 64;                            // [128] by sum - 2 lev0
-  float* fvd = (float*)(A.big + kDirW);                 // [13][27], after the rows are read
+  float* fvd = (float*)(A.big + Lay::kW);               // [13][27], after the rows are read
   int* mn = (int*)(A.big + A.L.mn);
   float* mres = (float*)(A.big + A.L.mres);
   float* slots = (float*)(A.big + A.L.slots);
@@ -1480,9 +1497,9 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
   __syncwarp();
   // the two orders of the level pairs: counting sort by value (difference
   // k <= 63, sum s - 2 lev0 <= 126), ties by pair index
-  int pk_[3], ps_[3];
+  int pk_[kRounds], ps_[kRounds];
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {
+  for (int r = 0; r < kRounds; ++r) {
     const int t = 32 * r + lane;
     pk_[r] = ps_[r] = -1;
     if (t < npairs) {
@@ -1493,7 +1510,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
     }
   }
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {  // class sizes: the leader of each group adds
+  for (int r = 0; r < kRounds; ++r) {  // class sizes: the leader of each group adds
     const bool v = pk_[r] >= 0;
     const unsigned act = __ballot_sync(kFull, v);
     if (v) {
@@ -1528,7 +1545,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
     __syncwarp();
   }
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {  // positions: class start + rank in pair order
+  for (int r = 0; r < kRounds; ++r) {  // positions: class start + rank in pair order
     const bool v = pk_[r] >= 0;
     const unsigned act = __ballot_sync(kFull, v);
     int posk = 0, poss = 0;
@@ -1551,9 +1568,9 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
     __syncwarp();
   }
   {  // mark the last position of every class
-    int fk[3], fs[3];
+    int fk[kRounds], fs[kRounds];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < kRounds; ++r) {
       const int p = 32 * r + lane;
       fk[r] = fs[r] = 0;
       if (p < npairs) {
@@ -1563,7 +1580,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
     }
     __syncwarp();
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < kRounds; ++r) {
       const int p = 32 * r + lane;
       if (p < npairs) {
         kpos[p] |= (uint8_t)fk[r];
@@ -1599,8 +1616,8 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
       }
     } else {
       const float fT = (float)T, fT2 = fT * fT, invT = __fdividef(1.f, fT);
-      uint16_t* mrow = mg + d * 13;
-      uint16_t* wrow = wt + d * kDirRow;
+      uint16_t* mrow = mg + d * Lay::kMgRow;
+      Cnt* wrow = wt + d * Lay::kRow;
       // marginals c_a = |L_a & fwd(V)| + |L_a & bwd(V)| (both lanes)
       unsigned m1 = 0, m2 = 0, pmask = 0;
       float hx = 0.f;
@@ -1621,13 +1638,24 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
         }
       }
       const int present = __popc(pmask);
-      const bool slot = want_mcc && present >= 2;
+      // more than kCapL present levels: the dense S - u u^T over the m
+      // compact levels goes to this warp's global scratch and the solve to
+      // the CTA pool (which writes mres[d]); else the register solve's slot
+      const bool many = want_mcc && present > kCapL;
+      const bool slot = want_mcc && present >= 2 && !many;
       float* P = slots + d * kSlot;
+      float* Sm = many ? pool->scratch + (size_t)d * kMCap * kMCap : nullptr;
       if (slot)
         for (int t = h; t < kSlot; t += 2) P[t] = 0.f;
+      if (many)
+        for (int t = h; t < m * m; t += 2) Sm[(t / m) * kMCap + t % m] = 0.f;
       if (!h) {
         mn[d] = slot ? present : 0;
         if (!slot) mres[d] = kNaNf;
+        if (many) {
+          const int ti = atomicAdd(pool->count, 1);
+          pool->tasks[ti] = (pool->warp << 16) | (d << 8) | m;
+        }
       }
       __syncwarp(pm);
       unsigned a1 = 0, e2 = 0, maxc = 0;
@@ -1665,7 +1693,12 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
             // an empty pair of present levels: q = p_a p_b enters MI, and
             // S - u u^T is dense there (-u_a u_b)
             mi0 += mult * (unsigned long long)cc;
-            if (slot) P[pk(kCapL, pa, pb)] = (float)(-cc) * rsqrtf((float)ca * (float)cb) * invT;
+            const float v = (float)(-cc) * rsqrtf((float)ca * (float)cb) * invT;
+            if (slot) P[pk(kCapL, pa, pb)] = v;
+            if (many) {
+              Sm[a * kMCap + b] = v;
+              Sm[b * kMCap + a] = v;
+            }
             continue;
           }
           const unsigned j = A.lev[b];
@@ -1678,7 +1711,14 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
           const long long ct = (long long)C * T;
           if (ct != cc)  // p = p_x p_y exactly contributes nothing
             mi += fm * __fdividef((float)cc, fT2) * kl_term(__fdividef((float)(ct - cc), (float)cc));
-          if (slot) P[pk(kCapL, pa, pb)] = (float)(ct - cc) * rsqrtf((float)ca * (float)cb) * invT;
+          {
+            const float v = (float)(ct - cc) * rsqrtf((float)ca * (float)cb) * invT;
+            if (slot) P[pk(kCapL, pa, pb)] = v;
+            if (many) {
+              Sm[a * kMCap + b] = v;
+              Sm[b * kMCap + a] = v;
+            }
+          }
           if (dbg_glcm) {
             int32_t* g = dbg_glcm + (size_t)d * w.ng * w.ng;
             g[(i - 1) * w.ng + (j - 1)] = C;
@@ -1803,18 +1843,21 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
   __syncwarp();
   // leave the region zero (the count-matrix path and the later families
   // expect it so)
-  for (int q = lane; q < kDirBytes / 16; q += 32) ((uint4*)A.big)[q] = make_uint4(0u, 0u, 0u, 0u);
+  for (int q = lane; q < Lay::kBytes / 16; q += 32) ((uint4*)A.big)[q] = make_uint4(0u, 0u, 0u, 0u);
   __syncwarp();
 }
 
 static __device__ void glcm_family(const Win& w, const Arena& A, const FrJob& job,
                                    int32_t* dbg_glcm, const FbPool* pool) {
   if (A.mc != kMCap) pool = nullptr;
-  if (w.m <= kDirLevels && A.mc == kMCap && A.L.mn >= kDirBytes && job.delta == 1 &&
-      job.agg != 1) {
-    if (w.s == 3) return glcm_dir_lanes<3>(w, A, job, dbg_glcm);
-    if (w.s == 5) return glcm_dir_lanes<5>(w, A, job, dbg_glcm);
-    if (w.s == 7) return glcm_dir_lanes<7>(w, A, job, dbg_glcm);
+  // the lane-per-direction path: windows in shared memory, distance 1,
+  // per-direction aggregation; more than kCapL present levels need the pool
+  const bool want_mcc = (job.families & kFamMCC) != 0;
+  if (A.mc == kMCap && A.L.mn >= 3648 && job.delta == 1 && job.agg != 1 &&
+      (w.m <= kCapL || pool != nullptr || !want_mcc)) {
+    if (w.s == 3 && w.m <= DirLayout<3>::kLv) return glcm_dir_lanes<3>(w, A, job, dbg_glcm, pool);
+    if (w.s == 5 && w.m <= DirLayout<5>::kLv) return glcm_dir_lanes<5>(w, A, job, dbg_glcm, pool);
+    if (w.s == 7 && w.m <= DirLayout<7>::kLv) return glcm_dir_lanes<7>(w, A, job, dbg_glcm, pool);
   }
   if (w.m <= 32 && job.delta == 1 && job.agg != 1) {
     if (w.s == 3) return glcm_family_impl<3>(w, A, job, dbg_glcm, pool);
