@@ -164,3 +164,41 @@ def test_drain_errors():
     with pytest.raises(_lib.FlashmapError) as e:
         fm.fr_h5_write_maps("/nonexistent-dir/x.h5", p, img, mask, _maps(1, 2, vox.size), bad)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("shape,chunk", [((1, 1, 1), None), ((3, 2, 5), (8, 8, 8)),
+                                         ((2, 9, 4), (1, 1, 1)), ((40, 3, 3), None)])
+def test_spatial_edge_shapes(tmp_path, shape, chunk):
+    # a single voxel, chunks larger than the volume (clamped), tiny chunks
+    # (grown to at most 64), a long thin volume
+    img, mask = _volume(11, shape, frac=1.0, hole=False)
+    vox = np.flatnonzero(mask.reshape(-1)).astype(np.int32)
+    p = fm.fr_map_params_init(shape[2], shape[1], shape[0], features=[0, 92, 100])
+    maps = _maps(12, 3, vox.size)
+    path = tmp_path / "edge.h5"
+    fm.fr_h5_write_maps(path, p, img, mask, maps, vox, codec="gzip", chunk=chunk)
+    f = h5read.File(path)
+    names = fm.fr_feature_names()
+    dense = _expected_dense(maps, vox, shape)
+    for r, k in enumerate([0, 92, 100]):
+        ds = f.root.members["maps"].members[names[k]]
+        assert all(c <= s for c, s in zip(ds.chunks, shape))
+        assert np.prod([-(-s // c) for s, c in zip(shape, ds.chunks)]) <= 64
+        np.testing.assert_array_equal(ds.data.view(np.uint32), dense[r].view(np.uint32))
+    np.testing.assert_array_equal(f.root.members["image"].data, img)
+
+
+def test_options_defaults_and_bad_options():
+    opt = _lib.H5Options()
+    assert _lib.load().fr_h5_options_init(opt) == 0
+    assert (opt.codec, opt.level, opt.shuffle, opt.threads) == (fm.FR_H5_GZIP, 4, 1, 0)
+    assert list(opt.chunk) == [0, 0, 0]
+    shape = (4, 4, 4)
+    img, mask = _volume(13, shape, hole=False)
+    vox = np.flatnonzero(mask.reshape(-1)).astype(np.int32)
+    p = fm.fr_map_params_init(4, 4, 4, features=[0])
+    for kw in (dict(codec="gzip", level=10), dict(codec="gzip", level=-1)):
+        with pytest.raises(_lib.FlashmapError) as e:
+            fm.fr_h5_write_maps("/nonexistent-dir/x.h5", p, img, mask, _maps(1, 1, vox.size), vox,
+                                **kw)
+        assert e.value.status == 1
