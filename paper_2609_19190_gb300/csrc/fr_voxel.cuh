@@ -172,12 +172,56 @@ __device__ __forceinline__ float lane_quot(float num, float den) {
 }
 
 // ------------------------------------------------------------------ sorting
+// Compare-exchange of keys i and i ^ j held in one lane's registers.
+__device__ __forceinline__ void cx_reg(uint32_t& lo_slot, uint32_t& hi_slot, bool up) {
+  const uint32_t mn = min(lo_slot, hi_slot), mx = max(lo_slot, hi_slot);
+  lo_slot = up ? mn : mx;
+  hi_slot = up ? mx : mn;
+}
+
 // Ascending sort of n keys in a[0..n), padded to P = next power of two with
-// 0xffffffff.  Warp-synchronous bitonic network (registers for P <= 32).
+// 0xffffffff.  Warp-synchronous bitonic network: in registers for P <= 128
+// (key 32 r + lane in register r of the lane; partners at distance < 32 by
+// shuffle, at 32 and 64 within the lane), in shared memory beyond.
 static __device__ void warp_sort(uint32_t* a, int n) {
   const int lane = lane_id();
   int P = 1;
   while (P < n) P <<= 1;
+  if (P > 32 && P <= 128) {
+    uint32_t x[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = 32 * r + lane;
+      x[r] = i < n ? a[i] : 0xffffffffu;
+    }
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        if (j == 64) {
+          cx_reg(x[0], x[2], ((lane) & k) == 0);
+          cx_reg(x[1], x[3], ((32 + lane) & k) == 0);
+        } else if (j == 32) {
+          cx_reg(x[0], x[1], ((lane) & k) == 0);
+          cx_reg(x[2], x[3], ((64 + lane) & k) == 0);
+        } else {
+          const bool lower = (lane & j) == 0;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const uint32_t y = __shfl_xor_sync(kFull, x[r], j);
+            const bool up = ((32 * r + lane) & k) == 0;
+            const uint32_t mn = min(x[r], y), mx = max(x[r], y);
+            x[r] = (lower == up) ? mn : mx;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = 32 * r + lane;
+      if (i < P) a[i] = x[r];
+    }
+    __syncwarp();
+    return;
+  }
   if (P <= 32) {
     uint32_t x = lane < n ? a[lane] : 0xffffffffu;
     for (int k = 2; k <= 32; k <<= 1) {
