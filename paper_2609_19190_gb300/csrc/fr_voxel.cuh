@@ -158,11 +158,20 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
          ((unsigned long long)l2 << 32) + ((unsigned long long)l3 << 48);
 }
 
+// 64-bit integers to float from two 32-bit conversions (these stay off the
+// FP64 pipe, which 64-bit conversions use; at most one extra rounding)
+__device__ __forceinline__ float u64_to_f32(unsigned long long x) {
+  return fmaf((float)(unsigned)(x >> 32), 4294967296.f, (float)(unsigned)x);
+}
+__device__ __forceinline__ float s64_to_f32(long long x) {  // |x| < 2^63
+  return x < 0 ? -u64_to_f32((unsigned long long)(-x)) : u64_to_f32((unsigned long long)x);
+}
+
 __device__ __forceinline__ float i128_to_f32(__int128 v) {
   const bool neg = v < 0;
   const unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
-  const float f = (float)(unsigned long long)(u >> 64) * 18446744073709551616.0f +
-                  (float)(unsigned long long)u;
+  const float f = fmaf(u64_to_f32((unsigned long long)(u >> 64)), 18446744073709551616.0f,
+                       u64_to_f32((unsigned long long)u));
   return neg ? -f : f;
 }
 
@@ -1803,16 +1812,16 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
           idn += __fdividef(fc, 1.f + __fdividef(fk, ngf));
           if (k) iv += __fdividef(fc, fk * fk);
         }
-        const float MI = (mi + __fdividef((float)mi0, fT2)) * 1.44269504088896341f;  // bits
+        const float MI = (mi + __fdividef(u64_to_f32(mi0), fT2)) * 1.44269504088896341f;  // bits
         const long long var_num = (long long)T * (long long)m2 - (long long)m1 * m1;
         fval[0] = __fdividef((float)a1, fT);
         fval[1] = __fdividef((float)m1, fT);
         fval[5] = __fdividef((float)dk2, fT);
-        fval[6] = lane_quot((float)((long long)T * (long long)a1 - (long long)m1 * m1),
-                            (float)var_num);
+        fval[6] = lane_quot(s64_to_f32((long long)T * (long long)a1 - (long long)m1 * m1),
+                            s64_to_f32(var_num));
         fval[7] = __fdividef((float)dk, fT);
         fval[8] = de;
-        fval[9] = __fdividef((float)((long long)T * (long long)dk2 - (long long)dk * dk), fT2);
+        fval[9] = __fdividef(s64_to_f32((long long)T * (long long)dk2 - (long long)dk * dk), fT2);
         fval[10] = __fdividef((float)e2, fT2);
         fval[11] = hxy;
         fval[12] = lane_quot(-MI, hx);
@@ -1823,7 +1832,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
         fval[17] = __fdividef(idn, fT);
         fval[18] = __fdividef(iv, fT);
         fval[19] = __fdividef((float)maxc, fT);
-        fval[22] = __fdividef((float)var_num, fT2);
+        fval[22] = __fdividef(s64_to_f32(var_num), fT2);
         fval[25] = __fdividef((float)dk, fT);
       } else {
         // sum distribution, the same way
@@ -1856,7 +1865,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
         fval[4] = __fdividef(ce2, fT * fT * fT);
         fval[20] = __fdividef((float)sk, fT);
         fval[21] = se;
-        fval[24] = __fdividef((float)((long long)T * (long long)sk2 - (long long)sk * sk), fT2);
+        fval[24] = __fdividef(s64_to_f32((long long)T * (long long)sk2 - (long long)sk * sk), fT2);
       }
     }
     // every direction's rows are read: the features may reuse them; each
