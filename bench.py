@@ -40,8 +40,8 @@ ALU_LANES_PER_SM = 128  # fp32/int32 lanes per Blackwell SM
 # keyed by the SHA-256 of the CUDA sources it was taken with; a source change
 # makes the figure stale and the bench reports null.
 NCU_TRAFFIC = {
-    # profiles/fr_map_kernel_ct_plain_ncu.md: 26.50 MB read + 75.07 MB written
-    ("ct_plain", "687ff5fe661a43609d89375d682a57427ea738ae699ffc3fd0eb80c953f9e602"): 101572352,
+    # profiles/fr_map_kernel_ct_plain_ncu.md: 26.58 MB read + 75.21 MB written
+    ("ct_plain", "b41bd1b714398db916155c4c8b8e8042c3adb81fbda718b7e3c50aaa3090efd4"): 101794816,
 }
 
 
