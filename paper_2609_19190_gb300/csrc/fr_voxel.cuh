@@ -2365,6 +2365,181 @@ __device__ void glrlm_dir_lanes(const Win& w, const Arena& A, int32_t* dbg_glrlm
   __syncwarp();
 }
 
+// GLRLM of windows of side 7 with at most kMCap levels (per-direction
+// aggregation), every count in registers: lanes d and d + 16 take direction
+// d.  As in glrlm_dir_lanes, E_d (voxels whose successor u + d has the same
+// level) is the pair's union over levels, the run starts are V minus
+// bwd(E_d), and R_1 = E_d, R_{j+1} = E_d & fwd(R_j) mark the voxels that
+// begin a chain of j + 1 equal levels.  The chain is walked once, j outer:
+// at step j each lane counts c_j(a) = |L_a & starts & R_j| for its levels
+// (a = h, h + 2, ...) and finishes the cells of length j, c_{j-1}(a) - c_j(a),
+// keeping only the previous count per level.  The cell sums factor by
+// length: the length weights (1/j^2, j^2) multiply per-length totals over
+// levels (count, count/i^2, count i^2), so a cell costs one subtraction,
+// one FMA, one integer multiply-add and its entropy term.  No run count is
+// stored; the region keeps only the level sets and per-level constants.
+constexpr int kRun7L = 0, kRun7Inv = 1536, kRun7I2 = 1664, kRun7F = 1792, kRun7Clear = 2688;
+
+template <int S>
+__device__ void glrlm_dir_regs(const Win& w, const Arena& A, int32_t* dbg_glrlm) {
+  using W = typename SliceT<S>::W;
+  constexpr int kQ = (kMCap + 1) / 2;  // levels per lane
+  static_assert(kMCap * S * (int)sizeof(W) <= kRun7Inv - kRun7L, "level sets");
+  static_assert(kRun7Inv + kMCap * 4 <= kRun7I2 && kRun7I2 + kMCap * 4 <= kRun7F, "tables");
+  static_assert(kRun7F + 13 * 17 * 4 <= kRun7Clear, "feature rows");
+  const int lane = lane_id();
+  const int m = w.m;
+  W* Lsm = (W*)(A.big + kRun7L);          // [m][S]
+  float* inv_i2 = (float*)(A.big + kRun7Inv);  // [m] 1 / i^2
+  unsigned* i2t = (unsigned*)(A.big + kRun7I2);  // [m] i^2
+  float* fvd = (float*)(A.big + kRun7F);       // [13][17] features
+  W Lm[S], Vm[S];
+  slice_masks<S>(w, A, Lm, Vm);
+  if (lane < m) {
+#pragma unroll
+    for (int z = 0; z < S; ++z) Lsm[lane * S + z] = Lm[z];
+    const unsigned i = A.lev[lane];
+    i2t[lane] = i * i;
+    inv_i2[lane] = __fdividef(1.f, (float)(i * i));
+  }
+  __syncwarp();
+  const int d = lane & 15, h = lane >> 4;
+  const unsigned pm = (1u << d) | (1u << (d + 16));
+  if (d < kNumDirs) {
+    int dz, dy, dx;
+    dir_of(d, dz, dy, dx);
+    const SliceDir<S> D(dz, dy, dx);
+    W E[S];
+#pragma unroll
+    for (int z = 0; z < S; ++z) E[z] = 0;
+    for (int a = h; a < m; a += 2) {
+      W la[S], fa[S];
+#pragma unroll
+      for (int z = 0; z < S; ++z) la[z] = Lsm[a * S + z];
+      D.fwd(la, fa);
+#pragma unroll
+      for (int z = 0; z < S; ++z) E[z] |= la[z] & fa[z];
+    }
+#pragma unroll
+    for (int z = 0; z < S; ++z) E[z] |= __shfl_xor_sync(pm, E[z], 16);
+    W st[S], R[S];
+    {
+      W T[S];
+      D.bwd(E, T);
+#pragma unroll
+      for (int z = 0; z < S; ++z) {
+        st[z] = Vm[z] & ~T[z];
+        R[z] = E[z];
+      }
+    }
+    // every run has exactly one start: the direction's run total
+    unsigned nr = 0;
+#pragma unroll
+    for (int z = 0; z < S; ++z) nr += (unsigned)popc_w<W>(st[z]);
+    unsigned prev[kQ];
+    unsigned glnu = 0, si = 0, si2 = 0, sj = 0, sj2 = 0, rlnu = 0;
+    float f_inv_i2 = 0.f, f_j = 0.f, f_j_inv_i2 = 0.f, f_j_i2 = 0.f, f_jj_inv_i2 = 0.f,
+          f_jj_i2 = 0.f, ent = 0.f;
+    // j = 0: runs starting at each level (the rows)
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int a = h + 2 * q;
+      unsigned c = 0;
+      if (a < m) {
+#pragma unroll
+        for (int z = 0; z < S; ++z) c += (unsigned)popc_w<W>(Lsm[a * S + z] & st[z]);
+        glnu += c * c;
+        const unsigned ii = i2t[a];
+        si2 += c * ii;
+        si += c * (unsigned)A.lev[a];
+        f_inv_i2 += (float)c * inv_i2[a];
+      }
+      prev[q] = c;
+    }
+#pragma unroll
+    for (int j = 1; j <= S; ++j) {
+      // X = starts that begin a chain of j + 1 (empty past the window side)
+      W X[S];
+      if (j < S) {
+#pragma unroll
+        for (int z = 0; z < S; ++z) X[z] = st[z] & R[z];
+      }
+      // cells of length j: prev - c_j
+      unsigned col = 0, ui2 = 0;
+      float tinv = 0.f;
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) {
+        const int a = h + 2 * q;
+        if (a < m) {
+          unsigned c = 0;
+          if (j < S) {
+#pragma unroll
+            for (int z = 0; z < S; ++z) c += (unsigned)popc_w<W>(Lsm[a * S + z] & X[z]);
+          }
+          const unsigned cnt = prev[q] - c;
+          prev[q] = c;
+          if (cnt) {
+            col += cnt;
+            ui2 += cnt * i2t[a];
+            tinv += (float)cnt * inv_i2[a];
+            ent += ent_term((int)cnt, (int)nr);
+            if (dbg_glrlm)
+              dbg_glrlm[((size_t)d * w.ng + (A.lev[a] - 1)) * w.s + (j - 1)] = (int)cnt;
+          }
+        }
+      }
+      const float fj2 = (float)(j * j), inv_j2 = 1.f / (float)(j * j);
+      const unsigned colt = col + __shfl_xor_sync(pm, col, 16);
+      rlnu += colt * colt;
+      sj += col * (unsigned)j;
+      sj2 += col * (unsigned)(j * j);
+      f_j += (float)col * inv_j2;
+      f_j_inv_i2 += tinv * inv_j2;
+      f_j_i2 += (float)ui2 * inv_j2;
+      f_jj_inv_i2 += tinv * fj2;
+      f_jj_i2 += (float)ui2 * fj2;
+      if (j + 1 < S) {
+        W T[S];
+        D.fwd(R, T);
+#pragma unroll
+        for (int z = 0; z < S; ++z) R[z] = E[z] & T[z];
+      }
+    }
+    // the pair's totals (rlnu is already the pair's)
+    glnu += __shfl_xor_sync(pm, glnu, 16);
+    si += __shfl_xor_sync(pm, si, 16);
+    si2 += __shfl_xor_sync(pm, si2, 16);
+    sj += __shfl_xor_sync(pm, sj, 16);
+    sj2 += __shfl_xor_sync(pm, sj2, 16);
+    float fs[7] = {f_j, f_inv_i2, f_j_inv_i2, f_j_i2, f_jj_inv_i2, f_jj_i2, ent};
+#pragma unroll
+    for (int k = 0; k < 7; ++k) fs[k] += __shfl_xor_sync(pm, fs[k], 16);
+    const float nvf = (float)w.nv;
+    float* row = fvd + d * 17;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int f = 8 * h + k;
+      row[f] = glrlm_feature(f, fs, nr, sj2, glnu, rlnu, si, si2, sj, nvf);
+    }
+  }
+  __syncwarp();
+  if (lane < 16) {
+    float s = 0.f, c = 0.f;
+    int n = 0;
+    for (int dd = 0; dd < kNumDirs; ++dd) {
+      const float v = fvd[dd * 17 + lane];
+      if (!isnan(v)) {
+        two_sum_add(s, c, v);
+        ++n;
+      }
+    }
+    A.fv[42 + lane] = n ? __fdividef(s + c, (float)n) : kNaNf;
+  }
+  __syncwarp();
+  for (int t = lane; t < kRun7Clear / 16; t += 32) ((uint4*)A.big)[t] = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp();
+}
+
 // merged: the 13 directions' runs go into one matrix, whose features are
 // taken once (RunPercentage over 13 N_v: each voxel lies on one run per
 // direction).
@@ -2373,6 +2548,7 @@ static __device__ void glrlm_family(const Win& w, const Arena& A, bool merged, i
     if (w.s == 3) return glrlm_dir_lanes<3>(w, A, dbg_glrlm);
     if (w.s == 5) return glrlm_dir_lanes<5>(w, A, dbg_glrlm);
   }
+  if (!merged && A.mc == kMCap && w.s == 7) return glrlm_dir_regs<7>(w, A, dbg_glrlm);
   if (!merged && w.m <= 16) {
     if (w.s == 3) return glrlm_masks_packed<3>(w, A, dbg_glrlm);
     if (w.s == 5) return glrlm_masks_packed<5>(w, A, dbg_glrlm);
