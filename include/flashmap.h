@@ -90,6 +90,13 @@ enum {
    * dependence count percentage, dependence count energy (IBSI) */
   FR_EXTRAS_BEGIN = 93, FR_FEATURES_END = 101
 };
+/* Scalar extraction reports one statistic more than mapping (Table 2:
+ * statistics 22 in the scalar benchmark column, 21 in the default spatial
+ * column; scalar benchmark total 102 = the 101 map features + 1): id 101,
+ * the standard deviation sqrt(m2) of the raw intensities (population, the
+ * square root of firstorder_Variance).  It has no map: fr_map_plan rejects a
+ * mask that selects it; fr_scalar_plan accepts ids 0..101. */
+enum { FR_SCALAR_STDDEV = 101, FR_NUM_SCALAR_FEATURES = 102 };
 
 /* Mapping parameters (the paper's settings object: feature families,
  * discretisation, VOI handling; "Software design and extraction modes"). */
@@ -107,6 +114,16 @@ typedef struct fr_map_params {
   int32_t device;           /* CUDA device ordinal                                */
   int32_t mask_on_device;   /* 1: the mask pointer is a device pointer; 0: host   */
   int32_t aggregation;      /* FR_AGG_AVERAGE (default) or FR_AGG_MERGED          */
+  /* Intensity range of the discretisation.  0 (default): the VOI's own
+   * minimum and maximum.  1: [range_min, range_max] as given, with each
+   * intensity clamped to it before its gray level is taken (raw intensities
+   * are used unclamped elsewhere).  A z-slab of one volume planned on its
+   * own (sharding across GPUs, section "Multi-GPU" of the design) passes the
+   * whole VOI's range, so every slab discretises as the whole volume does
+   * and the slabs' maps reassemble the whole volume's maps exactly. */
+  int32_t range_given;      /* 0 or 1                                             */
+  int32_t range_min;        /* int16 value, <= range_max (range_given = 1)        */
+  int32_t range_max;        /* int16 value                                        */
 } fr_map_params;
 
 /* Launch shape of the mapping kernel (the autotuner's knobs).  Zero fields
@@ -193,6 +210,21 @@ fr_status fr_debug_matrices(fr_plan* plan, const int16_t* image,
                             const int32_t* cols, int32_t n, int32_t ng,
                             int32_t* rec, fr_stream_t s);
 
+/* Testing hook of failure detection (no GPU fault is made): every device
+ * wait of the mapping kernel is bounded in time, and a wait that runs out
+ * records FR_ERR_TIMEOUT in the plan's status word and makes every CTA leave
+ * (after its own copies in flight have landed).  After this call, runs of
+ * the plan bound each wait by wait_limit_ns (0 = the default, 10 s) and,
+ * when item >= 0, the feeder leaves the halo buffer of work item `item`
+ * unfilled: it issues no copy for it and never completes the buffer's
+ * barrier, so the waits on that buffer run out and fr_map_sync_status
+ * returns FR_ERR_TIMEOUT; the outputs of such a run are undefined.  item =
+ * -1 restores normal runs; the status word is cleared at the start of every
+ * run, so the next normal run is unaffected.  Errors: INVALID_ARG for item
+ * outside -1 .. (work items - 1) or a negative limit.  Host-side only; takes
+ * effect from the next fr_map_run. */
+fr_status fr_debug_wait_fault(fr_plan* plan, int32_t item, int64_t wait_limit_ns);
+
 /* Device time in milliseconds of the mapping kernel of the plan's last run,
  * measured by CUDA events the library records on the launching stream
  * immediately before and after that kernel (the discretisation and packing
@@ -224,7 +256,8 @@ void fr_batch_destroy(fr_batch* b);
  * extraction modes"): the selected features of the whole VOI, one value per
  * feature -- the map value of a window that covers every VOI voxel (so
  * kernel_radius plays no part).  Same parameters, discretisation,
- * aggregation and feature ids as mapping.  Counts are exact integers; the
+ * aggregation and feature ids as mapping, plus id 101 (FR_SCALAR_STDDEV),
+ * the statistic of Table 2's scalar column that has no map.  Counts are exact integers; the
  * features are computed in FP64 (MCC in FP32).
  *
  * fr_scalar_plan: discretisation plan and whole-VOI count buffers (about
@@ -234,9 +267,9 @@ void fr_batch_destroy(fr_batch* b);
  *   double [n_features] (selected features in id order), caller-owned, on the
  *   device.  Asynchronous on s; one run at a time per plan.  Device errors
  *   (Ng > 255 for FBW) are reported by fr_scalar_sync_status, and the outputs
- *   are then NaN.  Zone sums visit a hash table whose slot order can depend
- *   on thread timing, so GLSZM values may differ in the last bits between
- *   runs; everything else is deterministic. */
+ *   are then NaN.  Results are bit-identical between runs: the GLSZM cell
+ *   sums, which visit a hash table whose slot order depends on thread
+ *   timing, are added as exact fixed-point integers. */
 typedef struct fr_scalar fr_scalar;
 fr_status fr_scalar_plan(const fr_map_params* p, const uint8_t* mask, fr_scalar** out);
 fr_status fr_scalar_run(fr_scalar* sp, const int16_t* image_dev, double* out_dev,
@@ -357,8 +390,9 @@ fr_status fr_h5_write_scalar(const char* path, const fr_map_params* p, const fr_
                              const double* values, int32_t n_values, const fr_h5_options* opt);
 
 /* Names and helpers. */
-int32_t fr_feature_count(void);
-const char* fr_feature_name(int32_t id); /* NULL outside 0..100 */
+int32_t fr_feature_count(void);        /* map features: FR_NUM_FEATURES */
+int32_t fr_scalar_feature_count(void); /* scalar features: FR_NUM_SCALAR_FEATURES */
+const char* fr_feature_name(int32_t id); /* NULL outside 0..101 (101: scalar only) */
 const char* fr_status_string(fr_status s);
 /* Direction i (0..12) as (dz, dy, dx); INVALID_ARG outside 0..12. */
 fr_status fr_direction(int32_t i, int32_t* dz, int32_t* dy, int32_t* dx);

@@ -31,7 +31,7 @@ const double kNaN = std::numeric_limits<double>::quiet_NaN();
 
 /* Feature names: PyRadiomics-style class_Feature names of the 93 maps the
  * paper benchmarks (Table 2, spatial benchmark column). */
-const char* const kNames[FRO_NUM_FEATURES] = {
+const char* const kNames[FRO_NUM_SCALAR_FEATURES] = {
     /* first order (18) */
     "firstorder_Energy", "firstorder_TotalEnergy", "firstorder_Entropy",
     "firstorder_Minimum", "firstorder_10Percentile", "firstorder_90Percentile",
@@ -84,7 +84,9 @@ const char* const kNames[FRO_NUM_FEATURES] = {
     "firstorder_MedianAbsoluteDeviation", "firstorder_CoefficientOfVariation",
     "firstorder_QuartileCoefficientOfDispersion", "glcm_SumVariance",
     "glcm_Dissimilarity", "gldm_GrayLevelNonUniformityNormalized",
-    "gldm_DependencePercentage", "gldm_DependenceEnergy"
+    "gldm_DependencePercentage", "gldm_DependenceEnergy",
+    /* scalar extraction only (id 101) */
+    "firstorder_StandardDeviation"
 };
 
 /* The 13 directions of 3-D texture analysis: one vector d of every +-d pair
@@ -964,6 +966,7 @@ bool params_ok(const fro_params* p) {
   if (p->disc_mode == FRO_FBW && !(p->bin_width > 0)) return false;
   if (p->disc_mode != FRO_FBN && p->disc_mode != FRO_FBW) return false;
   if (p->aggregation != FRO_AGG_AVERAGE && p->aggregation != FRO_AGG_MERGED) return false;
+  if (p->range_given && p->range_min > p->range_max) return false;
   return true;
 }
 
@@ -974,7 +977,7 @@ extern "C" {
 int32_t fro_feature_count(void) { return FRO_NUM_FEATURES; }
 
 const char* fro_feature_name(int32_t id) {
-  return (id >= 0 && id < FRO_NUM_FEATURES) ? kNames[id] : nullptr;
+  return (id >= 0 && id < FRO_NUM_SCALAR_FEATURES) ? kNames[id] : nullptr;
 }
 
 void fro_direction(int32_t i, int32_t* dz, int32_t* dy, int32_t* dx) {
@@ -1006,6 +1009,10 @@ int32_t fro_discretise(const fro_params* p, const int16_t* img,
       ++count;
     }
   if (count == 0) return 1;
+  if (p->range_given) {
+    xmin = p->range_min;
+    xmax = p->range_max;
+  }
   int ng;
   double anchor = xmin;
   if (p->disc_mode == FRO_FBN) {
@@ -1022,15 +1029,17 @@ int32_t fro_discretise(const fro_params* p, const int16_t* img,
       continue;
     }
     int g;
+    /* a given range: the intensity clamped to it */
+    const int x = p->range_given ? std::min(std::max((int)img[i], xmin), xmax) : (int)img[i];
     if (p->disc_mode == FRO_FBN) {
       if (xmax == xmin) {
         g = 1;
       } else {
-        g = (int)(((int64_t)ng * (img[i] - xmin)) / (xmax - xmin)) + 1;
+        g = (int)(((int64_t)ng * (x - xmin)) / (xmax - xmin)) + 1;
         if (g > ng) g = ng;
       }
     } else {
-      g = (int)std::floor(((double)img[i] - anchor) / p->bin_width) + 1;
+      g = (int)std::floor(((double)x - anchor) / p->bin_width) + 1;
     }
     levels[i] = (uint8_t)g;
   }
@@ -1070,6 +1079,19 @@ int32_t fro_scalar(const fro_params* p, const int16_t* img, const uint8_t* level
   if (!any) return 1;
   Cube c = make_whole_cube(p, img, levels);
   map_one(&q, c, ng, out);
+  /* standard deviation: sqrt((1/N) sum (x - mean)^2) over the raw
+   * intensities of the VOI (population form, as firstorder_Variance) */
+  double sum = 0.0, n = 0.0;
+  for (size_t k = 0; k < c.lev.size(); ++k)
+    if (c.lev[k]) {
+      sum += c.raw[k];
+      n += 1.0;
+    }
+  const double mean = sum / n;
+  double ss = 0.0;
+  for (size_t k = 0; k < c.lev.size(); ++k)
+    if (c.lev[k]) ss += (c.raw[k] - mean) * (c.raw[k] - mean);
+  out[101] = std::sqrt(ss / n);
   return 0;
 }
 

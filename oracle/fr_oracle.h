@@ -48,6 +48,10 @@ enum { FRO_ANCHOR_VOI_MIN = 0, FRO_ANCHOR_ZERO_FLOOR = 1 };
 enum { FRO_AGG_AVERAGE = 0, FRO_AGG_MERGED = 1 };
 
 #define FRO_NUM_FEATURES 101
+/* Scalar extraction adds the one statistic of Table 2's scalar column that
+ * has no map (statistics 22 there against 21 in the default spatial column):
+ * id 101, the standard deviation (population) of the raw intensities. */
+#define FRO_NUM_SCALAR_FEATURES 102
 #define FRO_NUM_BENCH 93
 #define FRO_NUM_DIRS 13
 
@@ -62,6 +66,9 @@ typedef struct fro_params {
   int32_t distance;          /* GLCM offset distance delta (>= 1)            */
   int32_t kurtosis_excess;   /* 1: m4/m2^2 - 3 ; 0: m4/m2^2                  */
   int32_t aggregation;       /* FRO_AGG_AVERAGE or FRO_AGG_MERGED            */
+  int32_t range_given;       /* 1: discretise over [range_min, range_max],   */
+  int32_t range_min;         /*    each intensity clamped to it (a z-slab of */
+  int32_t range_max;         /*    one volume, discretised as the whole VOI) */
 } fro_params;
 
 /* Number of features and the name of feature id (0..92). */
@@ -85,12 +92,13 @@ int32_t fro_map_voxels(const fro_params* p, const int16_t* img,
                        const uint8_t* levels, int32_t ng, const int64_t* vox,
                        int64_t n, double* out, int32_t nthreads);
 
-/* Scalar extraction: the 101 features of the whole VOI (the paper's other
- * extraction mode; the map value at v equals it whenever the window around v
- * covers the VOI).  levels from fro_discretise; p->radius is ignored.
- * Returns 0, 1 for an empty VOI, 3 for invalid parameters. */
+/* Scalar extraction: the 102 features of the whole VOI (the paper's other
+ * extraction mode; ids 0..100 equal the map value at v whenever the window
+ * around v covers the VOI, id 101 is the scalar-only standard deviation).
+ * levels from fro_discretise; p->radius is ignored.  Returns 0, 1 for an
+ * empty VOI, 3 for invalid parameters. */
 int32_t fro_scalar(const fro_params* p, const int16_t* img, const uint8_t* levels,
-                   int32_t ng, double* out101);
+                   int32_t ng, double* out102);
 
 /* Dense texture matrices of one voxel's sub-VOI V(v) (bit-exact integers).
  * glcm  : [13][ng][ng]  symmetric co-occurrence counts (levels 1..ng at 0..ng-1)

@@ -12,6 +12,7 @@ import numpy as np
 from . import build as _build
 
 NUM_FEATURES = 101
+NUM_SCALAR_FEATURES = 102
 NUM_BENCH = 93  # ids 0..92: the spatial benchmark set
 NUM_DIRS = 13
 FBN, FBW = 0, 1
@@ -27,12 +28,13 @@ class Params(C.Structure):
         ("bin_width", C.c_double), ("fbw_anchor", C.c_int32),
         ("radius", C.c_int32), ("distance", C.c_int32),
         ("kurtosis_excess", C.c_int32), ("aggregation", C.c_int32),
+        ("range_given", C.c_int32), ("range_min", C.c_int32), ("range_max", C.c_int32),
     ]
 
 
 def make_params(shape, *, disc_mode=FBN, bin_count=16, bin_width=25.0,
                 fbw_anchor=ANCHOR_VOI_MIN, radius=1, distance=1,
-                spacing=(1.0, 1.0, 1.0), kurtosis_excess=1, aggregation=0):
+                spacing=(1.0, 1.0, 1.0), kurtosis_excess=1, aggregation=0, value_range=None):
     nz, ny, nx = shape
     p = Params()
     p.nx, p.ny, p.nz = nx, ny, nz
@@ -41,6 +43,8 @@ def make_params(shape, *, disc_mode=FBN, bin_count=16, bin_width=25.0,
     p.fbw_anchor, p.radius, p.distance = fbw_anchor, radius, distance
     p.kurtosis_excess = kurtosis_excess
     p.aggregation = aggregation
+    if value_range is not None:
+        p.range_given, p.range_min, p.range_max = 1, int(value_range[0]), int(value_range[1])
     return p
 
 
@@ -82,6 +86,11 @@ def _ptr(a):
 def feature_names():
     L = lib()
     return [L.fro_feature_name(i).decode() for i in range(NUM_FEATURES)]
+
+
+def scalar_feature_names():
+    L = lib()
+    return [L.fro_feature_name(i).decode() for i in range(NUM_SCALAR_FEATURES)]
 
 
 def directions():
@@ -134,10 +143,11 @@ def map_volume(params, image, mask, nthreads=0):
 
 
 def scalar(params, image, levels, ng):
-    """The 101 features of the whole VOI (scalar extraction)."""
+    """The 102 features of the whole VOI (scalar extraction): the 101 map
+    features and the scalar-only standard deviation (id 101)."""
     image = np.ascontiguousarray(image, dtype=np.int16)
     levels = np.ascontiguousarray(levels, dtype=np.uint8)
-    out = np.empty(NUM_FEATURES)
+    out = np.empty(NUM_SCALAR_FEATURES)
     rc = lib().fro_scalar(C.byref(params), _ptr(image), _ptr(levels), ng, _ptr(out))
     if rc != 0:
         raise OracleError("fro_scalar failed with code %d" % rc)

@@ -19,6 +19,7 @@ import ctypes as C
 from . import _lib
 from ._lib import (FR_ANCHOR_VOI_MIN, FR_ANCHOR_ZERO_FLOOR, FR_FBN, FR_FBW,  # noqa: F401
                    FR_H5_GZIP, FR_H5_LZF, FR_H5_NONE, FR_NUM_DIRECTIONS, FR_NUM_FEATURES,
+                   FR_NUM_SCALAR_FEATURES, FR_SCALAR_STDDEV,
                    FlashmapError, MapParams, Tune, check)
 
 __all__ = [
@@ -28,7 +29,7 @@ __all__ = [
     "fr_plan_last_kernel_ms", "fr_batch_last_kernel_ms",
     "fr_batch_run", "fr_batch_sync_status", "fr_batch_query", "fr_batch_destroy",
     "fr_feature_names", "fr_direction", "FR_FBN", "FR_FBW", "MapParams", "Tune",
-    "FlashmapError", "fr_h5_write_maps", "fr_h5_write_scalar",
+    "FlashmapError", "fr_h5_write_maps", "fr_h5_write_scalar", "fr_debug_wait_fault",
 ]
 
 FAMILIES = {
@@ -71,6 +72,9 @@ def fr_map_params_init(nx, ny, nz, **fields):
     sp = fields.pop("spacing", None)
     if sp is not None:
         p.spacing[:] = list(sp)
+    vr = fields.pop("value_range", None)  # (min, max) of the discretisation
+    if vr is not None:
+        p.range_given, p.range_min, p.range_max = 1, int(vr[0]), int(vr[1])
     for k, v in fields.items():
         if not hasattr(p, k):
             raise AttributeError("fr_map_params has no field %r" % k)
@@ -78,8 +82,8 @@ def fr_map_params_init(nx, ny, nz, **fields):
     return p
 
 
-def selected_features(params):
-    return [f for f in range(FR_NUM_FEATURES)
+def selected_features(params, n=FR_NUM_FEATURES):
+    return [f for f in range(n)
             if (params.feature_mask[f >> 6] >> (f & 63)) & 1]
 
 
@@ -164,7 +168,7 @@ class ScalarPlan:
         check("fr_scalar_query", _lib.load().fr_scalar_query(handle, C.byref(n_voi), C.byref(nf),
                                                               C.byref(nbytes)))
         self.n_voi, self.n_features, self.device_bytes = n_voi.value, nf.value, nbytes.value
-        self.features = selected_features(params)
+        self.features = selected_features(params, FR_NUM_SCALAR_FEATURES)
 
     def __del__(self):
         try:
@@ -247,6 +251,14 @@ def fr_scatter_dense(plan, out, stream=None):
     check("fr_scatter_dense", _lib.load().fr_scatter_dense(
         plan.handle, C.c_void_p(out.data_ptr()), C.c_void_p(dense.data_ptr()), _stream_ptr(stream)))
     return dense
+
+
+def fr_debug_wait_fault(plan, item, wait_limit_ns=0):
+    """Testing hook of the bounded device waits: later runs of the plan
+    leave work item `item`'s halo buffer unfilled (-1: none) and bound every
+    wait by wait_limit_ns (0: the default)."""
+    check("fr_debug_wait_fault", _lib.load().fr_debug_wait_fault(plan.handle, int(item),
+                                                                 int(wait_limit_ns)))
 
 
 def fr_debug_matrices(plan, image, cols, ng, stream=None):

@@ -19,6 +19,8 @@ FR_FBN, FR_FBW = 0, 1
 FR_ANCHOR_VOI_MIN, FR_ANCHOR_ZERO_FLOOR = 0, 1
 FR_NUM_FEATURES = 101
 FR_NUM_BENCH_FEATURES = 93  # ids 0..92: the benchmark maps (the default selection)
+FR_SCALAR_STDDEV = 101  # scalar extraction only: the standard deviation (no map)
+FR_NUM_SCALAR_FEATURES = 102
 FR_NUM_DIRECTIONS = 13
 FR_H5_NONE, FR_H5_GZIP, FR_H5_LZF = 0, 1, 2
 
@@ -33,6 +35,7 @@ class MapParams(C.Structure):
         ("feature_mask", C.c_uint64 * 2),
         ("kurtosis_excess", C.c_int32), ("device", C.c_int32),
         ("mask_on_device", C.c_int32), ("aggregation", C.c_int32),
+        ("range_given", C.c_int32), ("range_min", C.c_int32), ("range_max", C.c_int32),
     ]
 
 
@@ -106,6 +109,8 @@ SIGNATURES = {
     "fr_h5_write_scalar": (C.c_int, [C.c_char_p, C.POINTER(MapParams), C.POINTER(H5Source), _P,
                                      C.c_int32, C.POINTER(H5Options)]),
     "fr_feature_count": (C.c_int32, []),
+    "fr_debug_wait_fault": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "fr_scalar_feature_count": (C.c_int32, []),
     "fr_feature_name": (C.c_char_p, [C.c_int32]),
     "fr_status_string": (C.c_char_p, [C.c_int]),
     "fr_direction": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),

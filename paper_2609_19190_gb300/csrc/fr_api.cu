@@ -53,7 +53,7 @@ namespace {
 
 // Feature names: PyRadiomics-style class_Feature names of the 93 spatial
 // benchmark maps (Table 2), in feature-id order.
-const char* const kFeatureNames[kNumFeatures] = {
+const char* const kFeatureNames[kNumScalarFeatures] = {
     "firstorder_Energy", "firstorder_TotalEnergy", "firstorder_Entropy",
     "firstorder_Minimum", "firstorder_10Percentile", "firstorder_90Percentile",
     "firstorder_Maximum", "firstorder_Mean", "firstorder_Median",
@@ -99,7 +99,9 @@ const char* const kFeatureNames[kNumFeatures] = {
     "firstorder_MedianAbsoluteDeviation", "firstorder_CoefficientOfVariation",
     "firstorder_QuartileCoefficientOfDispersion", "glcm_SumVariance", "glcm_Dissimilarity",
     "gldm_GrayLevelNonUniformityNormalized", "gldm_DependencePercentage",
-    "gldm_DependenceEnergy"
+    "gldm_DependenceEnergy",
+    // scalar extraction only (no map)
+    "firstorder_StandardDeviation"
 };
 
 // Directions (dz, dy, dx) in the documented order.
@@ -146,7 +148,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-bool valid_params(const fr_map_params* p) {
+// nfeat: ids below it may be selected (maps: kNumFeatures; scalar
+// extraction: kNumScalarFeatures).
+bool valid_params(const fr_map_params* p, int nfeat = kNumFeatures) {
   if (!p) return false;
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return false;
   if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return false;
@@ -163,11 +167,15 @@ bool valid_params(const fr_map_params* p) {
   }
   if (!(p->spacing[0] > 0 && p->spacing[1] > 0 && p->spacing[2] > 0)) return false;
   if (p->aggregation != FR_AGG_AVERAGE && p->aggregation != FR_AGG_MERGED) return false;
+  if (p->range_given != 0 && p->range_given != 1) return false;
+  if (p->range_given && (p->range_min < -32768 || p->range_max > 32767 ||
+                         p->range_min > p->range_max))
+    return false;
   bool any = false;
-  for (int f = 0; f < kNumFeatures; ++f)
+  for (int f = 0; f < nfeat; ++f)
     if ((p->feature_mask[f >> 6] >> (f & 63)) & 1ull) any = true;
   if (!any) return false;
-  if ((p->feature_mask[1] >> (kNumFeatures - 64)) != 0ull) return false;
+  if ((p->feature_mask[1] >> (nfeat - 64)) != 0ull) return false;
   return true;
 }
 
@@ -227,10 +235,10 @@ struct JobRes {
   }
 };
 
-void select_features(JobRes& j) {
+void select_features(JobRes& j, int nfeat) {
   int row = 0;
   j.families = kFamFO;
-  for (int f = 0; f < kNumFeatures; ++f) {
+  for (int f = 0; f < nfeat; ++f) {
     bool on = (j.p.feature_mask[f >> 6] >> (f & 63)) & 1ull;
     j.row_of[f] = on ? (int16_t)row++ : (int16_t)-1;
     if (!on) continue;
@@ -243,16 +251,16 @@ void select_features(JobRes& j) {
     if (f >= kGlcmExtra && f < kGldmExtra) j.families |= kFamGLCM;
     if (f >= kGldmExtra && f < kNumFeatures) j.families |= kFamGLDM;
   }
-  for (int f = kNumFeatures; f < kRowOf; ++f) j.row_of[f] = -1;
+  for (int f = nfeat; f < kRowOf; ++f) j.row_of[f] = -1;
   j.nf = row;
   j.ngc = j.p.disc_mode == FR_FBN ? j.p.bin_count : 255;
 }
 
 // Build the VOI list, brick schedule and items of one mask (synchronous).
 fr_status build_job(const fr_map_params* p, const uint8_t* mask, const fr_tune& tune,
-                    JobRes& j, cudaStream_t s) {
+                    JobRes& j, cudaStream_t s, int nfeat = kNumFeatures) {
   j.p = *p;
-  select_features(j);
+  select_features(j, nfeat);
   const int nx = p->nx, ny = p->ny, nz = p->nz;
   const int rows = ny * nz;
   const int64_t nvox = (int64_t)nx * ny * nz;
@@ -343,6 +351,8 @@ struct Engine {
   void** run_ptrs_dev = nullptr;
   FrItem* items_dev = nullptr;
   int n_items = 0;
+  int64_t timeout_ns = kTimeoutNs;  // bound of every device wait
+  int32_t withhold_item = -1;       // testing hook (fr_debug_wait_fault)
   uint32_t* queue = nullptr;
   int32_t* status = nullptr;
   char* slab = nullptr;
@@ -408,7 +418,8 @@ struct Engine {
     a.arena = arena;
     a.dbg = nullptr;
     a.dbg_stride = 0;
-    a.timeout_ns = kTimeoutNs;
+    a.timeout_ns = timeout_ns;
+    a.withhold_item = withhold_item;
     (void)dump;
     return a;
   }
@@ -483,6 +494,9 @@ struct Engine {
         h.disc_mode = j.p.disc_mode;
         h.bin_count = j.p.bin_count;
         h.anchor_zero_floor = j.p.fbw_anchor == FR_ANCHOR_ZERO_FLOOR;
+        h.range_given = j.p.range_given ? 1 : 0;
+        h.range_min = j.p.range_min;
+        h.range_max = j.p.range_max;
         h.kurt_excess = j.p.kurtosis_excess ? 1 : 0;
         h.nf = j.nf;
         h.families = j.families;
@@ -788,7 +802,7 @@ struct fr_scalar {
 namespace {
 
 fr_status scalar_open(fr_scalar& S, const fr_map_params* p, const uint8_t* mask) {
-  if (!valid_params(p) || !mask) return FR_ERR_INVALID_ARG;
+  if (!valid_params(p, kNumScalarFeatures) || !mask) return FR_ERR_INVALID_ARG;
   S.device = p->device;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || S.device < 0 || S.device >= ndev)
@@ -800,7 +814,7 @@ fr_status scalar_open(fr_scalar& S, const fr_map_params* p, const uint8_t* mask)
   S.sms = prop.multiProcessorCount;
   cudaStream_t s = nullptr;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return FR_ERR_CUDA;
-  fr_status st = build_job(p, mask, default_tune(nullptr), S.j, s);
+  fr_status st = build_job(p, mask, default_tune(nullptr), S.j, s, kNumScalarFeatures);
   if (st != FR_OK) {
     cudaStreamDestroy(s);
     return st;
@@ -824,6 +838,9 @@ fr_status scalar_open(fr_scalar& S, const fr_map_params* p, const uint8_t* mask)
     h.disc_mode = p->disc_mode;
     h.bin_count = p->bin_count;
     h.anchor_zero_floor = p->fbw_anchor == FR_ANCHOR_ZERO_FLOOR;
+    h.range_given = p->range_given ? 1 : 0;
+    h.range_min = p->range_min;
+    h.range_max = p->range_max;
     h.kurt_excess = p->kurtosis_excess ? 1 : 0;
     h.nf = j.nf;
     h.families = j.families;
@@ -982,6 +999,14 @@ fr_status fr_map_run_host(fr_plan* plan, const int16_t* image_host, float* out_h
     return FR_ERR_CUDA;
   if (cudaStreamSynchronize(cs) != cudaSuccess) return FR_ERR_CUDA;
   return E.sync_status();
+}
+
+fr_status fr_debug_wait_fault(fr_plan* plan, int32_t item, int64_t wait_limit_ns) {
+  if (!plan || item < -1 || item >= plan->E.n_items || wait_limit_ns < 0)
+    return FR_ERR_INVALID_ARG;
+  plan->E.withhold_item = item;
+  plan->E.timeout_ns = wait_limit_ns > 0 ? wait_limit_ns : kTimeoutNs;
+  return FR_OK;
 }
 
 fr_status fr_map_sync_status(fr_plan* plan) {
@@ -1330,6 +1355,9 @@ fr_status fr_server_add(fr_server* S, const fr_map_params* p, const uint8_t* mas
     h.disc_mode = j.p.disc_mode;
     h.bin_count = j.p.bin_count;
     h.anchor_zero_floor = j.p.fbw_anchor == FR_ANCHOR_ZERO_FLOOR;
+    h.range_given = j.p.range_given ? 1 : 0;
+    h.range_min = j.p.range_min;
+    h.range_max = j.p.range_max;
     h.kurt_excess = j.p.kurtosis_excess ? 1 : 0;
     h.nf = j.nf;
     h.families = j.families;
@@ -1432,6 +1460,7 @@ fr_status fr_server_step(fr_server* S, int64_t voxel_budget, int32_t* n_active) 
   a.fb_stride = S->fb_stride;
   a.arena = S->arena;
   a.timeout_ns = kTimeoutNs;
+  a.withhold_item = -1;
   const int grid = std::min(S->grid, a.n_items);
   if (fr_map_launch(false, a, grid, S->smem, S->stream) != cudaSuccess) return FR_ERR_CUDA;
   if (cudaEventRecord(st.ev, S->stream) != cudaSuccess) return FR_ERR_CUDA;
@@ -1515,8 +1544,10 @@ void fr_server_destroy(fr_server* S) {
 
 int32_t fr_feature_count(void) { return kNumFeatures; }
 
+int32_t fr_scalar_feature_count(void) { return kNumScalarFeatures; }
+
 const char* fr_feature_name(int32_t id) {
-  return (id >= 0 && id < kNumFeatures) ? kFeatureNames[id] : nullptr;
+  return (id >= 0 && id < kNumScalarFeatures) ? kFeatureNames[id] : nullptr;
 }
 
 const char* fr_status_string(fr_status s) {

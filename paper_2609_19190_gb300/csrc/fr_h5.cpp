@@ -717,9 +717,9 @@ std::vector<Attr> root_attrs(const fr_map_params* p, const fr_h5_source* src, co
   return a;
 }
 
-std::vector<int64_t> selected_ids(const fr_map_params* p) {
+std::vector<int64_t> selected_ids(const fr_map_params* p, int nfeat) {
   std::vector<int64_t> ids;
-  for (int f = 0; f < FR_NUM_FEATURES; ++f)
+  for (int f = 0; f < nfeat; ++f)
     if ((p->feature_mask[f >> 6] >> (f & 63)) & 1ull) ids.push_back(f);
   return ids;
 }
@@ -754,7 +754,7 @@ fr_status fr_h5_write_maps(const char* path, const fr_map_params* p, const fr_h5
   Codec c;
   if (!check_common(path, p, src, opt, &c) || !maps || !voxel_index || n_voi < 1)
     return FR_ERR_INVALID_ARG;
-  const std::vector<int64_t> ids = selected_ids(p);
+  const std::vector<int64_t> ids = selected_ids(p, FR_NUM_FEATURES);
   if ((int32_t)ids.size() != n_rows || n_rows < 1) return FR_ERR_INVALID_ARG;
   if (c.codec == FR_H5_GZIP && !zlib().ok) return FR_ERR_UNSUPPORTED;
   const uint64_t dims[3] = {(uint64_t)p->nz, (uint64_t)p->ny, (uint64_t)p->nx};
@@ -850,7 +850,7 @@ fr_status fr_h5_write_scalar(const char* path, const fr_map_params* p, const fr_
                              const double* values, int32_t n_values, const fr_h5_options* opt) {
   Codec c;
   if (!check_common(path, p, src, opt, &c) || !values) return FR_ERR_INVALID_ARG;
-  const std::vector<int64_t> ids = selected_ids(p);
+  const std::vector<int64_t> ids = selected_ids(p, FR_NUM_SCALAR_FEATURES);
   if ((int32_t)ids.size() != n_values || n_values < 1) return FR_ERR_INVALID_ARG;
   if (c.codec == FR_H5_GZIP && !zlib().ok) return FR_ERR_UNSUPPORTED;
   const uint64_t dims[3] = {(uint64_t)p->nz, (uint64_t)p->ny, (uint64_t)p->nx};

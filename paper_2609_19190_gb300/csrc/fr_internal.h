@@ -14,7 +14,12 @@ constexpr int kNumBench = 93;
 constexpr int kFirstExtra = 93;  // median abs. deviation, CoV, QCoD
 constexpr int kGlcmExtra = 96;   // sum variance, dissimilarity
 constexpr int kGldmExtra = 98;   // GLNUN, dependence count percentage, energy
-constexpr int kRowOf = 104;      // row_of entries (>= kNumFeatures)
+// Scalar extraction adds one statistic that has no map: the standard
+// deviation (Table 2: statistics 22 in the scalar benchmark column, 21 in
+// the default spatial column), id 101.
+constexpr int kScalarStd = 101;
+constexpr int kNumScalarFeatures = 102;
+constexpr int kRowOf = 104;      // row_of entries (>= kNumScalarFeatures)
 constexpr int kScalarDirF = 42;  // per-direction values of the scalar path
 constexpr int kNumDirs = 13;
 constexpr int kMaxRadius = 7;
@@ -68,6 +73,7 @@ struct alignas(128) FrJob {
   int32_t hx;  // x halo of the TMA box (multiple of 4, >= r)
   int32_t box_x, box_y, box_z;
   int32_t disc_mode, bin_count, anchor_zero_floor;
+  int32_t range_given, range_min, range_max;  // given discretisation range
   int32_t kurt_excess;
   int32_t agg;  // FR_AGG_AVERAGE / FR_AGG_MERGED
   int32_t nf;  // output rows
@@ -121,6 +127,7 @@ struct FrMapArgs {
   int32_t* dbg;        // debug records (DUMP kernel only)
   int64_t dbg_stride;  // int32 per record
   int64_t timeout_ns;  // bound of every device wait
+  int32_t withhold_item;  // testing: the feeder leaves this item's buffer unfilled (-1: none)
 };
 
 // Scalar extraction (the whole VOI as one region): device buffers and sizes.

@@ -91,6 +91,9 @@ __device__ __noinline__ void feed(const FrMapArgs& args, Feeder& fd, int stage,
     mbar_arrive(&fd.full[stage]);
     return;
   }
+  // testing hook of the bounded waits: no copy and no arrival, so the
+  // buffer's phase never completes and every wait on it runs out
+  if (it == args.withhold_item) return;
   const FrItem& item = args.items[it];
   const FrJob& job = args.jobs[item.job];
   const CUtensorMap* tm = &job.tmap;
@@ -139,7 +142,7 @@ __device__ void map_voxel(const FrMapArgs& args, const FrJob& job,
     const int cy = y - item.by;
     const int cz = z - item.bz;
     w.nv = gather_window(w, A, tile, job.box_x, job.box_y, cx, cy, cz);
-    warp_sort(A.kb, w.nv);
+    warp_sort_x(A.kb, w.nv, (int*)(A.tmp + 32));
     if (DUMP) {
       const int ng = w.ng;
       int32_t* rec = args.dbg + (size_t)it * args.dbg_stride;

@@ -9,6 +9,9 @@
 //        a = floor(xmin / w) * w (zero-floor anchor); Ng = floor((xmax - a)
 //        / w) + 1.  Explicit round-to-nearest intrinsics keep the compiler
 //        from contracting these into FMAs.
+// With a given range (a z-slab of one volume discretised as the whole VOI),
+// xmin / xmax are the given bounds and each intensity is clamped to them
+// before its level is taken; the packed word keeps the raw intensity.
 #include <climits>
 #include <cstdint>
 
@@ -24,8 +27,9 @@ __global__ void fr_reset_kernel(const FrJob* jobs, int njobs, uint32_t* queue,
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < njobs) {
     FrJobState* st = jobs[j].state;
-    st->xmin = INT_MAX;
-    st->xmax = INT_MIN;
+    const bool given = jobs[j].range_given != 0;
+    st->xmin = given ? jobs[j].range_min : INT_MAX;
+    st->xmax = given ? jobs[j].range_max : INT_MIN;
     st->ng = 0;
     st->status = 0;
   }
@@ -38,6 +42,7 @@ __global__ void fr_reset_kernel(const FrJob* jobs, int njobs, uint32_t* queue,
 // VOI intensity range: grid (blocks per job, jobs).
 __global__ void fr_minmax_kernel(const FrJob* jobs, void* const* run_ptrs) {
   const FrJob& job = jobs[blockIdx.y];
+  if (job.range_given) return;
   const int16_t* img = (const int16_t*)run_ptrs[2 * blockIdx.y];
   int lo = INT_MAX, hi = INT_MIN;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < job.n_voi;
@@ -80,7 +85,8 @@ __global__ void fr_pack_kernel(const FrJob* jobs, void* const* run_ptrs) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < job.n_voi;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int lin = job.voi[k];
-    const int v = img[lin];
+    const int raw = img[lin];
+    const int v = job.range_given ? min(max(raw, xmin), xmax) : raw;
     int g;
     if (job.disc_mode == 0) {
       if (xmax == xmin) {
@@ -95,7 +101,7 @@ __global__ void fr_pack_kernel(const FrJob* jobs, void* const* run_ptrs) {
     const int x = lin % job.nx;
     const int rest = lin / job.nx;  // z * ny + y
     job.packed[(size_t)rest * job.px + x] =
-        ((uint32_t)(v + 32768) << 8) | (uint32_t)g;
+        ((uint32_t)(raw + 32768) << 8) | (uint32_t)g;
   }
 }
 

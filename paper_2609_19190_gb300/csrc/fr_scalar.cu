@@ -99,6 +99,58 @@ __device__ void block_sum_u64(unsigned long long (&v)[K], unsigned long long* sh
   __syncthreads();
 }
 
+// Fixed-point terms for sums whose order of addition varies between runs
+// (the zone table's slot order depends on thread timing): x >= 0 times 2^fb,
+// truncated to an unsigned 128-bit integer.  Integer sums do not depend on
+// the order of addition, so the total is the same on every run.  The caller
+// keeps x < 2^(127 - fb).
+__device__ __forceinline__ unsigned __int128 sc_fixed(double x, int fb) {
+  if (!(x > 0.0)) return 0;
+  int e;
+  const double m = frexp(x, &e);  // x = m 2^e, 0.5 <= m < 1
+  const unsigned long long mi = (unsigned long long)ldexp(m, 53);  // exact
+  const int sh = e - 53 + fb;
+  if (sh >= 0) return (unsigned __int128)mi << sh;
+  if (sh <= -64) return 0;
+  return (unsigned __int128)(mi >> (-sh));
+}
+__device__ __forceinline__ double sc_unfixed(unsigned __int128 v, int fb) {
+  const double hi = (double)(unsigned long long)(v >> 64), lo = (double)(unsigned long long)v;
+  return ldexp(hi, 64 - fb) + ldexp(lo, -fb);
+}
+
+// Block sum of K unsigned 128-bit integers (exact); sh holds K * 32 values.
+template <int K>
+__device__ void block_sum_u128(unsigned __int128 (&v)[K], unsigned __int128* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  auto shfl = [](unsigned __int128 x, int o) {
+    const unsigned long long lo = __shfl_xor_sync(kFull, (unsigned long long)x, o);
+    const unsigned long long hi = __shfl_xor_sync(kFull, (unsigned long long)(x >> 64), o);
+    return ((unsigned __int128)hi << 64) | lo;
+  };
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v[k] += shfl(v[k], o);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k * 32 + warp] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      unsigned __int128 x = lane < nw ? sh[k * 32 + lane] : (unsigned __int128)0;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) x += shfl(x, o);
+      if (lane == 0) sh[k * 32] = x;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = sh[k * 32];
+  __syncthreads();
+}
+
 __device__ __forceinline__ double sc_ent(double p) { return p > 0.0 ? -p * log2(p) : 0.0; }
 __device__ __forceinline__ double sc_div(double a, double b) {
   return b == 0.0 ? __longlong_as_double(0x7ff8000000000000ll) : a / b;
@@ -544,6 +596,7 @@ __global__ void __launch_bounds__(kScThreads) sc_glrlm_feat_kernel(const __grid_
 __global__ void __launch_bounds__(kMiscThreads) sc_misc_feat_kernel(const __grid_constant__ FrScalarArgs a) {
   __shared__ double s_red[12 * 32];
   __shared__ unsigned long long s_ured[4 * 32];
+  __shared__ unsigned __int128 s_qred[11 * 32];
   __shared__ unsigned long long s_base[kMiscThreads];
   __shared__ int s_val[10];
   __shared__ int s_mm[2];
@@ -554,6 +607,7 @@ __global__ void __launch_bounds__(kMiscThreads) sc_misc_feat_kernel(const __grid
   if (sc_failed(a)) {
     if (blockIdx.x == 0 && tid < 18) out[tid] = kNaN;
     if (blockIdx.x == 0 && tid < 3) out[kFirstExtra + tid] = kNaN;
+    if (blockIdx.x == 0 && tid == 0) out[kScalarStd] = kNaN;
     if (blockIdx.x == 1 && tid < 16) out[58 + tid] = kNaN;
     if (blockIdx.x == 2 && tid < 19) out[74 + tid] = kNaN;
     if (blockIdx.x == 2 && tid < 3) out[kGldmExtra + tid] = kNaN;
@@ -693,6 +747,8 @@ __global__ void __launch_bounds__(kMiscThreads) sc_misc_feat_kernel(const __grid
       out[kFirstExtra] = m[6] / N;
       out[kFirstExtra + 1] = sc_div(sqrt(m2), mean);
       out[kFirstExtra + 2] = sc_div(p75 - p25, p75 + p25);
+      // standard deviation (population), the scalar-only statistic
+      out[kScalarStd] = sqrt(m2);
     }
   } else if (blockIdx.x == 1) {
     // ---- GLSZM from zones per level, per size and per (level, size)
@@ -713,26 +769,29 @@ __global__ void __launch_bounds__(kMiscThreads) sc_misc_feat_kernel(const __grid
     block_sum<2>(m, s_red);
     const double N = (double)u[0];
     const double mui = m[0] / N, muj = m[1] / N;
-    double v[11];
-    for (int k = 0; k < 11; ++k) v[k] = 0.0;
+    // every (level, size) cell's terms, summed in fixed point so that the
+    // slot order of the zone table does not change the result.  Bits after
+    // the point per sum, from its bound (I <= 255, J < 2^31, sum p = 1):
+    // <= 1 -> 120; <= 255^2 -> 110; <= 2^62 -> 64; <= 2^78 -> 48.
+    constexpr int kFb[11] = {120, 64, 110, 64, 120, 120, 110, 120, 110, 64, 48};
+    unsigned __int128 q[11];
+    for (int k = 0; k < 11; ++k) q[k] = 0;
     for (int64_t t = tid; t < a.hcap; t += blockDim.x) {
       const unsigned long long key = a.hkey[t];
       if (key == kEmptyKey) continue;
       const double I = (double)(key >> 32), J = (double)(key & 0xffffffffull);
       const double p = (double)a.hcnt[t] / N;
-      v[0] += p / (J * J);
-      v[1] += p * J * J;
-      v[2] += (I - mui) * (I - mui) * p;
-      v[3] += (J - muj) * (J - muj) * p;
-      v[4] += sc_ent(p);
-      v[5] += p / (I * I);
-      v[6] += p * I * I;
-      v[7] += p / (I * I * J * J);
-      v[8] += p * I * I / (J * J);
-      v[9] += p * J * J / (I * I);
-      v[10] += p * I * I * J * J;
+      const double tv[11] = {p / (J * J),          p * J * J,          (I - mui) * (I - mui) * p,
+                             (J - muj) * (J - muj) * p, sc_ent(p),     p / (I * I),
+                             p * I * I,            p / (I * I * J * J), p * I * I / (J * J),
+                             p * J * J / (I * I),  p * I * I * J * J};
+#pragma unroll
+      for (int k = 0; k < 11; ++k) q[k] += sc_fixed(tv[k], kFb[k]);
     }
-    block_sum<11>(v, s_red);
+    block_sum_u128<11>(q, s_qred);
+    double v[11];
+#pragma unroll
+    for (int k = 0; k < 11; ++k) v[k] = sc_unfixed(q[k], kFb[k]);
     if (tid == 0) {
       double* f = out + 58;
       if (u[0] == 0) {
@@ -899,7 +958,7 @@ __global__ void sc_final_kernel(const __grid_constant__ FrScalarArgs a, double* 
     a.out[k < 24 ? 18 + k : k < 40 ? 42 + (k - 24) : kGlcmExtra + (k - 40)] = c ? s / c : kNaN;
   }
   __syncthreads();
-  for (int f = threadIdx.x; f < kNumFeatures; f += blockDim.x) {
+  for (int f = threadIdx.x; f < kNumScalarFeatures; f += blockDim.x) {
     const int row = row_of_dev[f];
     if (row >= 0) user_out[row] = bad ? kNaN : a.out[f];
   }

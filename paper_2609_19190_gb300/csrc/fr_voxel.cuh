@@ -265,6 +265,93 @@ static __device__ void warp_sort(uint32_t* a, int n) {
   }
 }
 
+// Ascending sort of the n window keys ((x + 32768) << 8 | level) in a[0..n)
+// by the intensity x alone: the level is a nondecreasing function of x, so
+// keys of equal x are equal words and this is the order of the whole words.
+// For 128 < n <= 32 kRadixRounds: least-significant-digit radix sort of
+// x - min(x) in 5-bit digits (one bucket per lane), as many passes as the
+// window's intensity range has bits (none when every x is equal).  Keys stay
+// in registers between passes; each pass counts digits (match_any leaders
+// add to hist), scans the 32 counts, and scatters round by round in order,
+// so every pass is stable.  hist: 32 ints of warp scratch.  Other n: the
+// bitonic network of warp_sort (in registers up to 128 keys, where it was
+// measured faster than these passes).
+constexpr int kRadixRounds = 16;
+static __device__ void warp_sort_x(uint32_t* a, int n, int* hist) {
+  if (n <= 128 || n > 32 * kRadixRounds) return warp_sort(a, n);
+  const int lane = lane_id();
+  const int rounds = (n + 31) >> 5;
+  uint32_t k[kRadixRounds];
+  unsigned lo = 0xffffffffu, hi = 0u;
+#pragma unroll
+  for (int r = 0; r < kRadixRounds; ++r) {
+    const int i = 32 * r + lane;
+    k[r] = 0u;
+    if (r < rounds && i < n) {
+      k[r] = a[i];
+      lo = min(lo, k[r] >> 8);
+      hi = max(hi, k[r] >> 8);
+    }
+  }
+  lo = __reduce_min_sync(kFull, lo);
+  hi = __reduce_max_sync(kFull, hi);
+  if (hi == lo) return;
+  const int bits = 32 - __clz(hi - lo);
+  const unsigned last = __ballot_sync(kFull, 32 * (rounds - 1) + lane < n);
+  for (int sh = 0; sh < bits; sh += 5) {
+    hist[lane] = 0;
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < kRadixRounds; ++r) {
+      if (r < rounds) {
+        const unsigned act = (r == rounds - 1) ? last : kFull;
+        if ((act >> lane) & 1u) {
+          const unsigned d = (((k[r] >> 8) - lo) >> sh) & 31u;
+          const unsigned peers = __match_any_sync(act, d);
+          if ((peers & lanemask_lt()) == 0) atomicAdd(&hist[d], __popc(peers));
+        }
+      }
+    }
+    __syncwarp();
+    {  // exclusive scan of the digit counts
+      const int c = hist[lane];
+      int inc = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+      }
+      __syncwarp();
+      hist[lane] = inc - c;
+      __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < kRadixRounds; ++r) {
+      if (r < rounds) {
+        const unsigned act = (r == rounds - 1) ? last : kFull;
+        const bool v = (act >> lane) & 1u;
+        unsigned d = 0u, peers = 0u;
+        if (v) {
+          d = (((k[r] >> 8) - lo) >> sh) & 31u;
+          peers = __match_any_sync(act, d);
+          a[hist[d] + __popc(peers & lanemask_lt())] = k[r];
+        }
+        __syncwarp();
+        if (v && (peers & lanemask_lt()) == 0) hist[d] += __popc(peers);
+        __syncwarp();
+      }
+    }
+    if (sh + 5 < bits) {
+#pragma unroll
+      for (int r = 0; r < kRadixRounds; ++r) {
+        const int i = 32 * r + lane;
+        if (r < rounds && i < n) k[r] = a[i];
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // first index in a[lo..hi) with a[i] >= key (a sorted)
 __device__ __forceinline__ int lower_bound_u32(const uint32_t* a, int lo, int hi,
                                                uint32_t key) {

@@ -63,3 +63,36 @@ def slab_plan(nz, radius, world, rank):
     z0 = rank * base + min(rank, extra)
     z1 = z0 + base + (1 if rank < extra else 0)
     return z0, z1, max(0, z0 - radius), min(nz, z1 + radius)
+
+
+def map_slab(image, mask, world, rank, value_range, device=0, stream=None, **params):
+    """Map this rank's z-slab of one volume through the library.
+
+    The slab and its halo (slab_plan) are planned on their own with the whole
+    VOI's intensity range `value_range` = (min, max) (global_range gives it
+    across ranks), so the slab discretises exactly as the whole volume does.
+    Returns float32 [rows, n_own] on the device: the columns of the VOI
+    voxels with own_z0 <= z < own_z1, in the whole volume's column order
+    (z-major), so the ranks' results concatenate to the whole volume's maps.
+    image: int16 numpy [nz, ny, nx]; mask: uint8 numpy; params: keyword
+    fields of fr_map_params (kernel_radius required)."""
+    import numpy as np
+    import torch
+
+    import paper_2609_19190_gb300 as fm
+    nz, ny, nx = image.shape
+    z0, z1, h0, h1 = slab_plan(nz, params["kernel_radius"], world, rank)
+    sub_mask = np.ascontiguousarray(mask[h0:h1])
+    before = int(np.count_nonzero(sub_mask[:z0 - h0]))
+    own = int(np.count_nonzero(sub_mask[z0 - h0:z1 - h0]))
+    p = fm.fr_map_params_init(nx, ny, h1 - h0, value_range=value_range, device=device, **params)
+    if own == 0:
+        rows = len(fm.selected_features(p))
+        return torch.empty((rows, 0), dtype=torch.float32, device="cuda:%d" % device)
+    plan = fm.fr_map_plan(p, torch.from_numpy(sub_mask))
+    img = torch.from_numpy(np.ascontiguousarray(image[h0:h1])).to("cuda:%d" % device)
+    out = fm.fr_map_run(plan, img, stream=stream)
+    fm.fr_map_sync_status(plan)
+    fm.fr_map_destroy(plan)
+    # columns are z-major, so the owned slices are one contiguous block
+    return out[:, before:before + own]

@@ -41,7 +41,7 @@ def _smooth_noise(rng, shape, sigma):
         sh = [1] * len(shape)
         sh[axis] = f.size
         gain = gain * g.reshape(sh)
-    field = np.fft.irfftn(spec * gain, s=shape).astype(np.float32)
+    field = np.fft.irfftn(spec * gain, s=shape, axes=tuple(range(len(shape)))).astype(np.float32)
     field -= field.mean()
     sd = field.std()
     return field / (sd if sd > 0 else 1.0)

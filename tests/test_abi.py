@@ -92,6 +92,11 @@ def test_invalid_arguments_are_rejected_without_a_device():
     assert L.fr_map_sync_status(None) == 1
     L.fr_map_destroy(None)
     L.fr_batch_destroy(None)
-    assert L.fr_feature_name(101) is None and L.fr_feature_count() == 101
+    assert L.fr_feature_name(102) is None and L.fr_feature_count() == 101
+    assert L.fr_scalar_feature_count() == 102
+    assert L.fr_feature_name(101) == b"firstorder_StandardDeviation"
+    # the scalar-only statistic has no map
+    p = fm.fr_map_params_init(2, 2, 2, features=[0, fm.FR_SCALAR_STDDEV])
+    assert L.fr_map_plan(C.byref(p), mask, None, C.byref(h)) == 1
     assert L.fr_feature_name(93) == b"firstorder_MedianAbsoluteDeviation"
     assert L.fr_status_string(3) == b"more than 255 gray levels"

@@ -1,7 +1,8 @@
 """The multi-rank host logic on CPU with two gloo ranks (no GPU): sharded
 independent VOIs and z-slab sharding with halos and a global intensity range
 reassemble exactly the single-process result (mapping done by the FP64
-oracle standing in for each rank's device work); slowest-rank timing."""
+oracle standing in for each rank's device work, with the same given
+discretisation range the library takes); slowest-rank timing."""
 import os
 import socket
 
@@ -33,18 +34,9 @@ def _volumes():
 
 def _map(img, mask, vox=None, rng_override=None):
     from oracle import oracle as O
-    p = O.make_params(img.shape, disc_mode=O.FBN, bin_count=8, radius=1)
-    if rng_override is None:
-        levels, ng, lo, hi = O.discretise(p, img, mask)
-    else:
-        # discretise with the given global range: pin the range by two extra
-        # VOI voxels carrying the global extremes, then drop them
-        lo, hi = rng_override
-        pad_img = np.concatenate([img.reshape(-1), [lo, hi]]).astype(np.int16).reshape(1, 1, -1)
-        pad_mask = np.concatenate([mask.reshape(-1), [1, 1]]).astype(np.uint8).reshape(1, 1, -1)
-        pp = O.make_params(pad_img.shape, disc_mode=O.FBN, bin_count=8, radius=1)
-        lev, ng, _, _ = O.discretise(pp, pad_img, pad_mask)
-        levels = lev.reshape(-1)[:-2].reshape(img.shape)
+    p = O.make_params(img.shape, disc_mode=O.FBN, bin_count=8, radius=1,
+                      value_range=rng_override)
+    levels, ng, lo, hi = O.discretise(p, img, mask)
     if vox is None:
         vox = np.flatnonzero(mask.reshape(-1))
     return O.map_voxels(p, img, levels, ng, vox, nthreads=1)

@@ -404,6 +404,10 @@ def test_ibsi_extras_closed_forms_and_identities():
     assert f[93] == pytest.approx(30 / 11, rel=1e-14)
     assert f[94] == pytest.approx(math.sqrt(10) / 5, rel=1e-14)
     assert f[95] == pytest.approx(0.5, rel=1e-14)
+    # the scalar-only standard deviation: the population variance of 0..10 is
+    # (11^2 - 1) / 12 = 10
+    assert f[101] == pytest.approx(math.sqrt(10), rel=1e-14)
+    assert f[101] == pytest.approx(math.sqrt(f[16]), rel=1e-14)
     # on random windows: sum variance = cluster tendency and dissimilarity =
     # difference average (identities of a symmetric GLCM), dependence count
     # percentage = 1 (every voxel has a dependence count), GLNUN = GLNU / N_v
@@ -548,7 +552,9 @@ def test_scalar_against_naive_whole_cube(kw):
     raw[:9, :11, :10] = img
     ref = NP.features_of_cube(cube, raw, ng, vvox=0.7 * 1.0 * 1.5,
                               merged=kw.get("aggregation", 0) == O.AGG_MERGED)
-    np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-9, equal_nan=True)
+    np.testing.assert_allclose(got[:101], ref, rtol=1e-9, atol=1e-9, equal_nan=True)
+    # the scalar-only statistic: numpy's population standard deviation
+    assert got[101] == pytest.approx(float(np.std(img[mask > 0].astype(np.float64))), rel=1e-12)
 
 
 def test_scalar_equals_every_map_value_when_windows_cover_the_voi():
@@ -560,7 +566,7 @@ def test_scalar_equals_every_map_value_when_windows_cover_the_voi():
     maps, vox, levels, ng = _oracle_maps(img, mask, **kw)
     sc = O.scalar(O.make_params(img.shape, **kw), img, levels, ng)
     for k in range(maps.shape[1]):
-        np.testing.assert_allclose(maps[:, k], sc, rtol=1e-12, atol=1e-12, equal_nan=True)
+        np.testing.assert_allclose(maps[:, k], sc[:101], rtol=1e-12, atol=1e-12, equal_nan=True)
 
 
 def test_map_flip_permutation_translation_equivariance():
@@ -599,3 +605,27 @@ def test_feature_names_are_the_101_default_maps():
         [21, 26, 16, 16, 17, 5]
     assert sorted(O.directions()) == sorted(
         d for d in itertools.product((-1, 0, 1), repeat=3) if d > (0, 0, 0))
+
+
+def test_given_discretisation_range():
+    # the VOI's own range given explicitly changes nothing; a z-slab given the
+    # whole VOI's range gets the whole volume's levels on its voxels; a
+    # narrower range clamps (FBN 4 over [10, 30]: x <= 10 -> 1, x >= 30 -> 4)
+    rng = np.random.default_rng(70)
+    img = rng.integers(-200, 200, size=(9, 6, 5)).astype(np.int16)
+    mask = (rng.random(img.shape) < 0.7).astype(np.uint8)
+    for kw in (dict(disc_mode=O.FBN, bin_count=7), dict(disc_mode=O.FBW, bin_width=30.0),
+               dict(disc_mode=O.FBW, bin_width=30.0, fbw_anchor=O.ANCHOR_ZERO_FLOOR)):
+        lev, ng, lo, hi = O.discretise(O.make_params(img.shape, **kw), img, mask)
+        lev2, ng2, _, _ = O.discretise(O.make_params(img.shape, value_range=(lo, hi), **kw),
+                                       img, mask)
+        assert ng2 == ng and np.array_equal(lev2, lev)
+        sub = slice(3, 7)
+        lev3, ng3, _, _ = O.discretise(O.make_params(img[sub].shape, value_range=(lo, hi), **kw),
+                                       img[sub], mask[sub])
+        assert ng3 == ng and np.array_equal(lev3, lev[sub])
+    x = np.array([[[0, 10, 15, 20, 25, 30, 99]]], np.int16)
+    lev, ng, _, _ = O.discretise(O.make_params(x.shape, disc_mode=O.FBN, bin_count=4,
+                                               value_range=(10, 30)), x, np.ones_like(x, np.uint8))
+    # g = floor(4 (x - 10) / 20) + 1 on the clamped x, top bin at x = 30
+    assert lev.reshape(-1).tolist() == [1, 1, 2, 3, 4, 4, 4] and ng == 4
