@@ -3,8 +3,10 @@
 
 A step maps one whole synthetic volume: discretisation, VOI packing and the
 mapping kernel (all 93 maps of every VOI voxel).  Default workload: the
-CT-like 128 x 128 x 64 volume with an ellipsoidal VOI of 200,336 voxels,
-fixed bin width 25 HU, kernel radius 2 (5^3 windows), GLCM distance 1.
+largest single-GPU configuration, the CT-like 256 x 256 x 128 volume with a
+VOI of three ellipsoids (2,014,083 voxels), fixed bin count 64, kernel radius
+3 (7^3 windows), GLCM distance 1; the 128 x 128 x 64 CT-like volume (200,336
+voxels, FBW 25 HU, r = 2) is timed as an extra leg.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl flashmap|reference]
 
@@ -36,13 +38,12 @@ METRIC = "voxel-features/s for 3D texture maps, batched vs plain; serving p50/p9
 UNIT = "voxel-features/s"
 ALU_LANES_PER_SM = 128  # fp32/int32 lanes per Blackwell SM
 
-# DRAM bytes (read + write) per launch of fr_map_kernel from an ncu capture,
-# keyed by the SHA-256 of the CUDA sources it was taken with; a source change
-# makes the figure stale and the bench reports null.
-NCU_TRAFFIC = {
-    # profiles/fr_map_kernel_ct_plain_ncu.md: 26.58 MB read + 75.21 MB written
-    ("ct_plain", "b41bd1b714398db916155c4c8b8e8042c3adb81fbda718b7e3c50aaa3090efd4"): 101794816,
-}
+# Counters of fr_map_kernel from ncu captures, keyed by workload and the
+# SHA-256 of the CUDA sources they were taken with (a source change makes
+# them stale and the bench reports null): DRAM bytes (read + write) per
+# launch, issue-slot utilisation and shared-memory pipe utilisation (% of
+# peak), as summarised under profiles/.
+NCU_COUNTERS = {}
 
 
 def parse():
@@ -51,19 +52,25 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="flashmap", choices=["flashmap", "reference"])
-    ap.add_argument("--workload", default="ct_plain",
+    ap.add_argument("--workload", default="ct_large",
                     choices=["ct_plain", "tiny", "ct_large", "paper_tiled"])
+    ap.add_argument("--extra-workloads", default="ct_plain",
+                    help="comma-separated workloads timed as extra legs (kernel only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-single-seconds", type=float, default=10.0)
     ap.add_argument("--tune", default="", help="brick_x,brick_y,brick_z,vpi,warps,stages")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-scalar", action="store_true")
     ap.add_argument("--no-drain", action="store_true")
     ap.add_argument("--batch-vois", type=int, default=64)
-    ap.add_argument("--served-requests", type=int, default=120)
-    ap.add_argument("--served-rates", default="10,50,100,200")
+    ap.add_argument("--small-vois", type=int, default=256)
+    ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--served-rates", default="5,10,20,50,100,200,400,1000")
+    ap.add_argument("--served-seconds", type=float, default=12.0,
+                    help="time limit per served rate")
     return ap.parse_args()
 
 
@@ -239,17 +246,45 @@ def max_over_ranks(v, world):
 
 
 # ------------------------------------------------------------------ batched / served
-def measure_batched(n_vois, dev, steps=3):
-    """64 CT-like 128x128x64 VOIs (log-uniform 4k-400k voxels, r in {1,2,3},
-    FBN 16/32/64, 93 maps): the plain path maps them one plan at a time; the
-    batched path maps all of them in one persistent launch (CUDA graph) with
-    the autotuner's launch shape.  Device time with CUDA events."""
+def _plain_ms(params, masks, images, outs, dev, steps):
+    """Device time (CUDA events) of mapping the VOIs one plan at a time."""
+    import torch
+    import paper_2609_19190_gb300 as fm
+    stream = torch.cuda.current_stream(dev)
+    plans = [fm.fr_map_plan(p, m) for p, m in zip(params, masks)]
+    for pl, im, o in zip(plans, images, outs):
+        fm.fr_map_run(pl, im, o)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        e0.record(stream)
+        for pl, im, o in zip(plans, images, outs):
+            fm.fr_map_run(pl, im, o)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    for pl in plans:
+        fm.fr_map_sync_status(pl)
+        fm.fr_map_destroy(pl)
+    return statistics.median(ms)
+
+
+def measure_batched(kind, n_vois, dev, steps=3):
+    """Many VOIs, plain against batched.  kind "mixed": 64 CT-like
+    128x128x64 VOIs (log-uniform 4k-400k voxels); kind "small": 256 VOIs of
+    4k-20k voxels in 64^3 CT-like volumes; r in {1,2,3}, FBN 16/32/64, 93
+    maps.  Plain maps them one plan at a time (4 kernels each: reset,
+    intensity range, discretise/pack, map); batched maps all of them in one
+    persistent launch (the same 4 kernels once, captured in a CUDA graph)
+    with the autotuner's launch shape.  Device time with CUDA events."""
     import torch
     import paper_2609_19190_gb300 as fm
     from paper_2609_19190_gb300 import autotune, synth
+    item = synth.batch_item if kind == "mixed" else synth.batch_small_item
     params, masks, images = [], [], []
     for i in range(n_vois):
-        img, mask, r, bins = synth.batch_item(i)
+        img, mask, r, bins = item(i)
         nz, ny, nx = img.shape
         params.append(fm.fr_map_params_init(nx, ny, nz, disc_mode=0, bin_count=bins,
                                             kernel_radius=r, device=dev.index or 0))
@@ -258,26 +293,12 @@ def measure_batched(n_vois, dev, steps=3):
     voxels = int(sum(int(m.sum()) for m in masks))
     tune, timings = autotune.pick(params, masks, images)
     stream = torch.cuda.current_stream(dev)
-    plans = [fm.fr_map_plan(p, m) for p, m in zip(params, masks)]
-    outs = [torch.empty((pl.n_rows, pl.n_voi), dtype=torch.float32, device=dev) for pl in plans]
-    for pl, im, o in zip(plans, images, outs):
-        fm.fr_map_run(pl, im, o)
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    plain_ms = []
-    for _ in range(steps):
-        e0.record(stream)
-        for pl, im, o in zip(plans, images, outs):
-            fm.fr_map_run(pl, im, o)
-        e1.record(stream)
-        e1.synchronize()
-        plain_ms.append(e0.elapsed_time(e1))
-    for pl in plans:
-        fm.fr_map_sync_status(pl)
-        fm.fr_map_destroy(pl)
+    outs = [torch.empty((93, int(m.sum())), dtype=torch.float32, device=dev) for m in masks]
+    tp = _plain_ms(params, masks, images, outs, dev, steps)
     b = fm.fr_batch_plan(params, masks, tune=tune)
     fm.fr_batch_run(b, images, outs)
     torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     batch_ms = []
     for _ in range(steps):
         e0.record(stream)
@@ -287,50 +308,71 @@ def measure_batched(n_vois, dev, steps=3):
         batch_ms.append(e0.elapsed_time(e1))
     fm.fr_batch_sync_status(b)
     fm.fr_batch_destroy(b)
-    tp, tb = statistics.median(plain_ms), statistics.median(batch_ms)
+    tb = statistics.median(batch_ms)
+    desc = ("%d CT-like 128x128x64 VOIs, log-uniform 4k-400k voxels" % n_vois if kind == "mixed"
+            else "%d VOIs of log-uniform 4k-20k voxels in 64^3 CT-like volumes" % n_vois)
     return {"value": voxels * 93 / (tb / 1e3), "unit": UNIT, "plain_value": voxels * 93 / (tp / 1e3),
             "vs_plain": tp / tb, "ms_batched": tb, "ms_plain": tp, "n_vois": n_vois,
-            "voxels": voxels, "tune": tune, "launches_per_batch": 4,
-            "workload": "%d CT-like 128x128x64 VOIs, log-uniform 4k-400k voxels, r in {1,2,3}, "
-                        "FBN 16/32/64, 93 maps; batched = one persistent launch in a CUDA graph"
-                        % n_vois}
+            "voxels": voxels, "tune": tune, "tune_timings_ms": timings,
+            "kernels": {"batched": 4, "plain": 4 * n_vois},
+            "workload": desc + ", r in {1,2,3}, FBN 16/32/64, 93 maps; batched = one persistent "
+                               "launch in a CUDA graph"}
 
 
-def measure_served(n_requests, rates, dev):
-    """Poisson request stream (log-normal sizes, median 50k voxels), CT-like
-    volumes resident on the device, admission by free HBM, continuous
-    batching through fr_server_*; throughput and latency percentiles per rate."""
+def measure_served(n_requests, rates, dev, time_limit):
+    """Poisson request stream (log-normal sizes, median 50k voxels, drawn
+    in turn from 256 request templates), CT-like volumes resident on the
+    device, admission by free HBM, continuous batching through fr_server_*;
+    throughput and latency percentiles per rate, each rate until n_requests
+    have finished or time_limit seconds have passed.  plain_value: the same
+    templates mapped one plan at a time (device time)."""
     import torch
+    import paper_2609_19190_gb300 as fm
     from paper_2609_19190_gb300 import serve, synth
-    reqs = synth.served_requests(n_requests, seed=200)
+    reqs = synth.served_requests(n_requests, seed=200, templates=256)
     images = {sh: torch.from_numpy(synth.ct_like(sh, 500 + k)).to(dev)
               for k, sh in enumerate(synth.SERVED_SHAPES)}
-    serve.serve(reqs[:8], images, rate=0.0, seed=0, device=dev.index or 0)  # warm-up
+    base = reqs[:256]
+    params = []
+    for rq in base:
+        nz, ny, nx = rq["shape"]
+        params.append(fm.fr_map_params_init(nx, ny, nz, kernel_radius=rq["radius"],
+                                            device=dev.index or 0, **rq["disc"]))
+    outs = [torch.empty((93, rq["n_voi"]), dtype=torch.float32, device=dev) for rq in base]
+    tp = _plain_ms(params, [torch.from_numpy(rq["mask"]) for rq in base],
+                   [images[rq["shape"]] for rq in base], outs, dev, 1)
+    del outs
+    plain = sum(rq["n_voi"] for rq in base) * 93 / (tp / 1e3)
+    serve.serve(reqs[:16], images, rate=0.0, seed=0, device=dev.index or 0)  # warm-up
     out = []
     for rate in rates:
         st = serve.serve(reqs, images, rate=rate, seed=3, voxel_budget=131072,
-                         device=dev.index or 0, time_limit=60)
-        out.append({"rate": rate, "throughput": st["throughput"], "p50_s": st["p50_s"],
+                         device=dev.index or 0, time_limit=time_limit)
+        out.append({"rate": rate, "throughput": st["throughput"],
+                    "vs_plain": st["throughput"] / plain, "p50_s": st["p50_s"],
                     "p99_s": st["p99_s"], "requests": st["requests"],
-                    "makespan_s": st["makespan_s"]})
-    return {"unit": UNIT, "requests_per_rate": n_requests, "rates": out,
+                    "makespan_s": st["makespan_s"], "steps": st["steps"]})
+    return {"unit": UNIT, "plain_value": plain, "requests_per_rate": n_requests,
+            "time_limit_s": time_limit, "rates": out,
             "workload": "Poisson arrivals; CT-like VOIs of log-normal size (median 50k voxels, "
-                        "sigma_ln 1, <= 2M), r in {1,2,3}, FBN 64 or FBW 25, 93 maps; "
-                        "continuous batching, 131072-voxel steps, admission by free HBM"}
+                        "sigma_ln 1, <= 2M; 256 templates drawn in turn), r in {1,2,3}, FBN 64 "
+                        "or FBW 25, 93 maps; continuous batching, 131072-voxel steps, "
+                        "admission by free HBM"}
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_rate(img, mask, kw, seconds, seed=11):
-    """Time the oracle (as it stands) on all host cores on a seeded sample of
-    the workload's VOI voxels sized to take about `seconds`."""
+def oracle_rate(img, mask, kw, seconds, seed=11, threads=None):
+    """Time the oracle (as it stands) on `threads` host cores (all by
+    default) on a seeded sample of the workload's VOI voxels sized to take
+    about `seconds`."""
     from oracle import oracle as O
     from paper_2609_19190_gb300 import synth
     op = O.make_params(img.shape, disc_mode=kw["disc_mode"], bin_count=kw.get("bin_count", 16),
                        bin_width=kw.get("bin_width", 25.0), radius=kw["kernel_radius"],
                        distance=kw["glcm_distance"])
     levels, ng, _, _ = O.discretise(op, img, mask)
-    cores = os.cpu_count() or 1
-    probe = synth.sample_voxels(mask, min(256 * cores, int(mask.sum())), seed)
+    cores = threads or os.cpu_count() or 1
+    probe = synth.sample_voxels(mask, min(64 * cores, int(mask.sum())), seed)
     t0 = time.perf_counter()
     O.map_voxels(op, img, levels, ng, probe, nthreads=cores)
     dt = max(time.perf_counter() - t0, 1e-3)
@@ -419,6 +461,46 @@ def measure_scalar(img, mask, kw, dev, steps):
             "launches_per_extraction": 13,
             "note": "whole-VOI scalar features of the same volume (window = VOI), FP64 "
                     "features from exact counts"}
+
+
+def measure_plain(name, dev, steps, warmup):
+    """An extra plain workload: device time per step (discretisation, packing
+    and mapping kernel; CUDA events, L2 flushed between steps), the mapping
+    kernel's own time and its window-op rate."""
+    import torch
+
+    import paper_2609_19190_gb300 as fm
+    img, mask, kw, desc = workload(name)
+    nz, ny, nx = img.shape
+    params = fm.fr_map_params_init(nx, ny, nz, device=dev.index or 0, **kw)
+    plan = fm.fr_map_plan(params, torch.from_numpy(mask))
+    img_dev = torch.from_numpy(img).to(dev)
+    out = torch.empty((plan.n_rows, plan.n_voi), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(warmup, 1)):
+        fm.fr_map_run(plan, img_dev, out)
+    fm.fr_map_sync_status(plan)
+    step_ms, kern_ms = [], []
+    for _ in range(max(steps, 3)):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fm.fr_map_run(plan, img_dev, out)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(fm.fr_plan_last_kernel_ms(plan))
+    fm.fr_map_sync_status(plan)
+    ops = algorithmic_ops(mask, kw["kernel_radius"], kw["glcm_distance"])
+    t = sum(step_ms) / len(step_ms) / 1e3
+    kmean = statistics.mean(kern_ms) / 1e3
+    res = {"workload": desc, "n_voi": plan.n_voi, "maps": plan.n_rows,
+           "value": plan.n_voi * plan.n_rows / t, "unit": UNIT, "ms_per_step": 1e3 * t,
+           "kernel_ms": 1e3 * kmean, "ops_per_launch": ops, "achieved_gops": ops / kmean / 1e9}
+    fm.fr_map_destroy(plan)
+    return res
 
 
 def measure_drain(plan, params, out, img, mask):
@@ -524,23 +606,38 @@ def run_flashmap(args):
     ops = algorithmic_ops(mask, kw["kernel_radius"], kw["glcm_distance"])
     kmean = statistics.mean(kern_ms) / 1e3
     achieved = ops / kmean / 1e9
-    peak = sms * ALU_LANES_PER_SM * sm_max * 1e6 / 1e9
-    traffic = NCU_TRAFFIC.get((args.workload, source_digest()))
+    nominal = sms * ALU_LANES_PER_SM * sm_max * 1e6 / 1e9
+    try:
+        add_ops, mad_ops, fma_ops = fm.fr_measure_alu_peak(local)
+        peak = max(add_ops, mad_ops, fma_ops) / 1e9
+        basis = ("measured lane-op issue, %d SMs, full occupancy, best of 3: int32 add %.1f, "
+                 "int32 multiply-add %.1f, fp32 FMA %.1f Gop/s; peak = the fastest pipe "
+                 "(nominal %d x %d lanes x %.0f MHz = %.1f Gop/s)"
+                 % (sms, add_ops / 1e9, mad_ops / 1e9, fma_ops / 1e9, sms, ALU_LANES_PER_SM,
+                    sm_max, nominal))
+    except Exception as e:  # the helper failed: the nominal figure, said so
+        peak, basis = nominal, "nominal (measurement failed: %s)" % e
+    counters = NCU_COUNTERS.get((args.workload, source_digest()), {})
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-            "frac": achieved / peak, "traffic": traffic,
+            "frac": achieved / peak, "traffic": counters.get("traffic"),
             "kernel": "fr_map_kernel", "kernel_ms": 1e3 * kmean,
-            "ops_per_launch": ops,
-            "peak_basis": "%d SMs x %d int32/fp32 lanes x %.0f MHz (measured max SM clock)"
-                          % (sms, ALU_LANES_PER_SM, sm_max),
+            "ops_per_launch": ops, "peak_basis": basis,
+            "issue_active_pct": counters.get("issue_active_pct"),
+            "shared_pipe_pct": counters.get("shared_pipe_pct"),
             "hbm_gbs_achieved": (img.nbytes + 4 * nf * n_voi + 4 * n_voi) / kmean / 1e9,
             "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    extra = {}
+    for name in [w for w in args.extra_workloads.split(",") if w and w != args.workload]:
+        extra[name] = measure_plain(name, dev, args.steps, args.warmup)
     batched = None
-    if not args.no_batched and args.workload == "ct_plain":
-        batched = measure_batched(args.batch_vois, dev)
+    if not args.no_batched:
+        batched = measure_batched("mixed", args.batch_vois, dev)
+        batched["small_vois"] = measure_batched("small", args.small_vois, dev)
     served = None
-    if not args.no_served and args.workload == "ct_plain":
+    if not args.no_served:
         served = measure_served(args.served_requests,
-                                [float(r) for r in args.served_rates.split(",")], dev)
+                                [float(r) for r in args.served_rates.split(",")], dev,
+                                args.served_seconds)
     scalar = None
     if not args.no_scalar:
         scalar = measure_scalar(img, mask, kw, dev, args.steps)
@@ -552,6 +649,11 @@ def run_flashmap(args):
         rate, cores, n, dt, _ = oracle_rate(img, mask, kw, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d seeded VOI voxels of the workload, all 93 maps, %.1f s" % (n, dt)}
+        rate1, _, n1, dt1, _ = oracle_rate(img, mask, kw, args.cpu_single_seconds, seed=12,
+                                           threads=1)
+        cpu["single_thread"] = {"value": rate1, "unit": UNIT, "cores": 1,
+                                "sample": "%d seeded VOI voxels, all 93 maps, %.1f s"
+                                          % (n1, dt1)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -564,6 +666,7 @@ def run_flashmap(args):
                                             "feeds the TMA halo copies",
                               "tune": tune}},
         "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+        "extra_workloads": extra,
         "batched": batched, "served": served, "scalar": scalar, "drain": drain,
         "gpu_launches": 4 * args.steps,
     }

@@ -305,6 +305,18 @@ fr_status fr_server_query(const fr_server* s, int32_t* active, int32_t* inflight
                           size_t* device_bytes);
 void fr_server_destroy(fr_server* s);
 
+/* Measured issue throughput of the 32-bit ALU pipes of `device` (a
+ * measurement helper for the roofline of the mapping kernel, which is bound
+ * by plain integer / logic / fp32 instruction issue; the paper has no
+ * counterpart).  Every thread of a full-occupancy grid runs 8 dependency
+ * chains of one operation: int32 adds, int32 multiply-adds, fp32 fused
+ * multiply-adds; the best of 3 timed launches (CUDA events) of each gives
+ * lane operations per second, one instruction counted as one operation.
+ * Takes about 100 ms; allocates 64 bytes.  Errors: INVALID_ARG (NULL
+ * outputs), UNSUPPORTED, CUDA. */
+fr_status fr_measure_alu_peak(int32_t device, double* int32_add_per_s, double* int32_mad_per_s,
+                              double* fp32_fma_per_s);
+
 /* Allocation-free VOI voxel list.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory -- callers whose
  * device memory already belongs to another allocator (a framework's caching

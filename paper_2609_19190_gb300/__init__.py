@@ -253,6 +253,15 @@ def fr_scatter_dense(plan, out, stream=None):
     return dense
 
 
+def fr_measure_alu_peak(device=0):
+    """(int32 add, int32 multiply-add, fp32 FMA) lane operations per second
+    measured on the device."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    check("fr_measure_alu_peak", _lib.load().fr_measure_alu_peak(int(device), C.byref(a),
+                                                                  C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
 def fr_debug_wait_fault(plan, item, wait_limit_ns=0):
     """Testing hook of the bounded device waits: later runs of the plan
     leave work item `item`'s halo buffer unfilled (-1: none) and bound every

@@ -109,6 +109,8 @@ SIGNATURES = {
     "fr_h5_write_scalar": (C.c_int, [C.c_char_p, C.POINTER(MapParams), C.POINTER(H5Source), _P,
                                      C.c_int32, C.POINTER(H5Options)]),
     "fr_feature_count": (C.c_int32, []),
+    "fr_measure_alu_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double)]),
     "fr_debug_wait_fault": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "fr_scalar_feature_count": (C.c_int32, []),
     "fr_feature_name": (C.c_char_p, [C.c_int32]),

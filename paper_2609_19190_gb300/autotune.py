@@ -2,9 +2,11 @@
 
 Times a small set of candidate shapes (brick, voxels per work item, consumer
 warps per CTA, halo stages) on the caller's own workload and keeps the
-fastest, cached by a key of (kernel radius, level-count bucket, feature
-families) in a JSON file (FLASHMAP_TUNE_CACHE, else
-~/.cache/flashmap_tune.json).  Every candidate gives bit-identical maps (the
+fastest, cached in a JSON file (FLASHMAP_TUNE_CACHE, else
+~/.cache/flashmap_tune.json) under a key of the batch's composition: the set
+of kernel radii, the level-count bucket, the feature families and the
+bucket of VOI sizes (a batch of many small VOIs wants finer work items than
+one of a few large ones).  Every candidate gives bit-identical maps (the
 per-voxel computation does not depend on the launch shape), so only time
 decides.
 """
@@ -14,6 +16,9 @@ import os
 CANDIDATES = (
     dict(brick_x=8, brick_y=4, brick_z=4, voxels_per_item=16, consumer_warps=16, stages=1),
     dict(brick_x=8, brick_y=4, brick_z=4, voxels_per_item=32, consumer_warps=16, stages=1),
+    dict(brick_x=8, brick_y=4, brick_z=4, voxels_per_item=16, consumer_warps=16, stages=2),
+    dict(brick_x=8, brick_y=4, brick_z=4, voxels_per_item=16, consumer_warps=16, stages=3),
+    dict(brick_x=8, brick_y=4, brick_z=4, voxels_per_item=8, consumer_warps=16, stages=2),
     dict(brick_x=16, brick_y=4, brick_z=4, voxels_per_item=16, consumer_warps=16, stages=1),
     dict(brick_x=8, brick_y=8, brick_z=4, voxels_per_item=16, consumer_warps=16, stages=1),
     dict(brick_x=8, brick_y=4, brick_z=4, voxels_per_item=16, consumer_warps=8, stages=1),
@@ -33,12 +38,20 @@ def _families(features):
     return fam
 
 
-def key_of(params):
+def key_of(params_list, sizes):
+    """Cache key of a batch: radii present, largest level-count bucket, the
+    union of feature families, and the power-of-two bucket of the median VOI
+    size."""
     import paper_2609_19190_gb300 as fm
-    ng = params.bin_count if params.disc_mode == fm.FR_FBN else 255
+    radii = sorted({p.kernel_radius for p in params_list})
+    ng = max(p.bin_count if p.disc_mode == fm.FR_FBN else 255 for p in params_list)
     bucket = 16 if ng <= 16 else 32 if ng <= 32 else 64 if ng <= 64 else 255
-    return "r%d_ng%d_f%d" % (params.kernel_radius, bucket,
-                             _families(fm.selected_features(params)))
+    fam = 0
+    for p in params_list:
+        fam |= _families(fm.selected_features(p))
+    med = sorted(sizes)[len(sizes) // 2]
+    return "r%s_ng%d_f%d_v%d" % ("".join(map(str, radii)), bucket, fam,
+                                 max(0, int(med).bit_length() - 1))
 
 
 def _load():
@@ -76,10 +89,10 @@ def _time_batch(params_list, masks, images, tune, reps=2):
 
 
 def pick(params_list, masks, images, candidates=CANDIDATES, use_cache=True):
-    """Best launch shape for a batch (the key of its largest VOI).  Returns
-    (tune dict, {candidate index: kernel ms})."""
+    """Best launch shape for a batch.  Returns (tune dict, {candidate index:
+    kernel ms})."""
     sizes = [int(m.sum()) for m in masks]
-    key = key_of(params_list[sizes.index(max(sizes))])
+    key = key_of(params_list, sizes)
     cache = _load() if use_cache else {}
     if key in cache:
         return dict(cache[key]["tune"]), cache[key].get("timings", {})

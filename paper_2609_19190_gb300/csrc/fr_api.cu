@@ -135,6 +135,28 @@ T* dev_alloc(size_t count, size_t* acct) {
   return (T*)p;
 }
 
+// Allocation from a stream-ordered memory pool on stream s (no device-wide
+// synchronisation, unlike cudaMalloc / cudaFree), or plain cudaMalloc when
+// pool is null.
+template <class T>
+T* dev_alloc_on(size_t count, size_t* acct, cudaMemPool_t pool, cudaStream_t s) {
+  if (!pool) return dev_alloc<T>(count, acct);
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMallocFromPoolAsync(&p, count * sizeof(T), pool, s);
+  if (e != cudaSuccess) throw CudaFail{FR_ERR_OOM};
+  if (acct) *acct += count * sizeof(T);
+  return (T*)p;
+}
+
+void dev_free_on(void* p, cudaMemPool_t pool, cudaStream_t s) {
+  if (!p) return;
+  if (pool)
+    cudaFreeAsync(p, s);
+  else
+    cudaFree(p);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -224,6 +246,18 @@ struct JobRes {
   std::vector<FrItem> items;  // job field = 0
   size_t bytes = 0;
 
+  // Stream-ordered release (buffers from a memory pool): freed once the work
+  // already queued on s has finished; the host does not wait.
+  void release_async(cudaStream_t s) {
+    cudaFreeAsync(packed, s);
+    cudaFreeAsync(voi, s);
+    cudaFreeAsync(bcols, s);
+    cudaFreeAsync(state, s);
+    packed = nullptr;
+    voi = bcols = nullptr;
+    state = nullptr;
+  }
+
   void release() {
     cudaFree(packed);
     cudaFree(voi);
@@ -257,8 +291,11 @@ void select_features(JobRes& j, int nfeat) {
 }
 
 // Build the VOI list, brick schedule and items of one mask (synchronous).
+// pool: allocate from this stream-ordered pool on s (the server's requests:
+// planning never synchronises the device); null: cudaMalloc.
 fr_status build_job(const fr_map_params* p, const uint8_t* mask, const fr_tune& tune,
-                    JobRes& j, cudaStream_t s, int nfeat = kNumFeatures) {
+                    JobRes& j, cudaStream_t s, int nfeat = kNumFeatures,
+                    cudaMemPool_t pool = nullptr) {
   j.p = *p;
   select_features(j, nfeat);
   const int nx = p->nx, ny = p->ny, nz = p->nz;
@@ -272,13 +309,13 @@ fr_status build_job(const fr_map_params* p, const uint8_t* mask, const fr_tune& 
   try {
     const uint8_t* m = mask;
     if (!p->mask_on_device) {
-      dmask = dev_alloc<uint8_t>(nvox, nullptr);
+      dmask = dev_alloc_on<uint8_t>(nvox, nullptr, pool, s);
       FR_TRY(cudaMemcpyAsync(dmask, mask, nvox, cudaMemcpyHostToDevice, s));
       m = dmask;
     }
-    rowcnt = dev_alloc<int32_t>(rows, nullptr);
-    rowoff = dev_alloc<int32_t>(rows, nullptr);
-    tot = dev_alloc<long long>(1, nullptr);
+    rowcnt = dev_alloc_on<int32_t>(rows, nullptr, pool, s);
+    rowoff = dev_alloc_on<int32_t>(rows, nullptr, pool, s);
+    tot = dev_alloc_on<long long>(1, nullptr, pool, s);
     FR_TRY(fr_launch_row_count(m, nx, rows, rowcnt, s));
     FR_TRY(fr_launch_scan(rowcnt, rowoff, rows, tot, s));
     long long n = 0;
@@ -286,19 +323,19 @@ fr_status build_job(const fr_map_params* p, const uint8_t* mask, const fr_tune& 
     FR_TRY(cudaStreamSynchronize(s));
     if (n == 0) throw CudaFail{FR_ERR_EMPTY_MASK};
     j.n_voi = n;
-    j.voi = dev_alloc<int32_t>(n, &j.bytes);
+    j.voi = dev_alloc_on<int32_t>(n, &j.bytes, pool, s);
     FR_TRY(fr_launch_voi_fill(m, nx, rows, rowoff, j.voi, s));
     const int bx = tune.brick_x, by = tune.brick_y, bz = tune.brick_z;
     const int nbx = (nx + bx - 1) / bx, nby = (ny + by - 1) / by, nbz = (nz + bz - 1) / bz;
     const int nb = nbx * nby * nbz;
-    bcount = dev_alloc<int32_t>(nb, nullptr);
-    boff = dev_alloc<int32_t>(nb, nullptr);
-    bfill = dev_alloc<int32_t>(nb, nullptr);
+    bcount = dev_alloc_on<int32_t>(nb, nullptr, pool, s);
+    boff = dev_alloc_on<int32_t>(nb, nullptr, pool, s);
+    bfill = dev_alloc_on<int32_t>(nb, nullptr, pool, s);
     FR_TRY(cudaMemsetAsync(bcount, 0, nb * sizeof(int32_t), s));
     FR_TRY(cudaMemsetAsync(bfill, 0, nb * sizeof(int32_t), s));
     FR_TRY(fr_launch_bricks(j.voi, n, nx, ny, bx, by, bz, nbx, nby, bcount, s));
     FR_TRY(fr_launch_scan(bcount, boff, nb, tot, s));
-    j.bcols = dev_alloc<int32_t>(n, &j.bytes);
+    j.bcols = dev_alloc_on<int32_t>(n, &j.bytes, pool, s);
     FR_TRY(fr_launch_brick_fill(j.voi, n, nx, ny, bx, by, bz, nbx, nby, boff, bfill, j.bcols,
                                 s));
     std::vector<int32_t> hc(nb), ho(nb);
@@ -322,9 +359,9 @@ fr_status build_job(const fr_map_params* p, const uint8_t* mask, const fr_tune& 
     }
     j.px = (nx + 3) / 4 * 4;
     const size_t packed_n = (size_t)j.px * ny * nz;
-    j.packed = dev_alloc<uint32_t>(packed_n, &j.bytes);
+    j.packed = dev_alloc_on<uint32_t>(packed_n, &j.bytes, pool, s);
     FR_TRY(cudaMemsetAsync(j.packed, 0, packed_n * sizeof(uint32_t), s));
-    j.state = dev_alloc<FrJobState>(1, &j.bytes);
+    j.state = dev_alloc_on<FrJobState>(1, &j.bytes, pool, s);
     FR_TRY(cudaMemsetAsync(j.state, 0, sizeof(FrJobState), s));
     FR_TRY(cudaStreamSynchronize(s));
   } catch (CudaFail& f) {
@@ -332,13 +369,13 @@ fr_status build_job(const fr_map_params* p, const uint8_t* mask, const fr_tune& 
     cudaStreamSynchronize(s);
     j.release();
   }
-  cudaFree(dmask);
-  cudaFree(rowcnt);
-  cudaFree(rowoff);
-  cudaFree(bcount);
-  cudaFree(boff);
-  cudaFree(bfill);
-  cudaFree(tot);
+  dev_free_on(dmask, pool, s);
+  dev_free_on(rowcnt, pool, s);
+  dev_free_on(rowoff, pool, s);
+  dev_free_on(bcount, pool, s);
+  dev_free_on(boff, pool, s);
+  dev_free_on(bfill, pool, s);
+  dev_free_on(tot, pool, s);
   return st;
 }
 
@@ -698,6 +735,7 @@ struct fr_server {
   int slab_ngc = 255;
   cudaStream_t stream = nullptr;       // steps
   cudaStream_t plan_stream = nullptr;  // request planning
+  cudaMemPool_t pool = nullptr;        // stream-ordered pool of request buffers
   uint32_t* prep_queue = nullptr;      // words the discretisation kernels reset,
   int32_t* prep_status = nullptr;      // kept apart from the steps' queue/status
   ServerStep steps[2];
@@ -732,6 +770,10 @@ void server_release_all(fr_server* S) {
   cudaFree(S->prep_status);
   if (S->stream) cudaStreamDestroy(S->stream);
   if (S->plan_stream) cudaStreamDestroy(S->plan_stream);
+  if (S->pool) {
+    cudaDeviceSynchronize();
+    cudaMemPoolDestroy(S->pool);
+  }
 }
 
 // Complete the oldest busy step if it has finished (or wait for it).
@@ -1282,6 +1324,20 @@ fr_status fr_server_create(int32_t device, int32_t max_radius, int32_t max_slots
     S->grid = S->sms * blocks;
     FR_TRY(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
     FR_TRY(cudaStreamCreateWithFlags(&S->plan_stream, cudaStreamNonBlocking));
+    // request buffers come from a pool of the server's own: planning and
+    // release order their allocations on streams and never wait for the
+    // device (cudaMalloc / cudaFree would drain the steps in flight); freed
+    // memory stays in the pool for the next requests
+    {
+      cudaMemPoolProps props;
+      memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = device;
+      FR_TRY(cudaMemPoolCreate(&S->pool, &props));
+      uint64_t keep = ~0ull;
+      FR_TRY(cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
     S->prep_queue = dev_alloc<uint32_t>(1, &S->bytes);
     S->prep_status = dev_alloc<int32_t>(1, &S->bytes);
     S->slab_stride = fr_align(fr_big_layout(S->slab_ngc, S->slab_ngc, S->arena.w_max).bytes, 256);
@@ -1327,7 +1383,7 @@ fr_status fr_server_add(fr_server* S, const fr_map_params* p, const uint8_t* mas
   if (cudaSetDevice(S->device) != cudaSuccess) return FR_ERR_CUDA;
   ServerReq* r = new (std::nothrow) ServerReq();
   if (!r) return FR_ERR_OOM;
-  fr_status st = build_job(p, mask, S->tune, r->job, S->plan_stream);
+  fr_status st = build_job(p, mask, S->tune, r->job, S->plan_stream, kNumFeatures, S->pool);
   if (st != FR_OK) {
     delete r;
     return st;
@@ -1510,8 +1566,8 @@ fr_status fr_server_release(fr_server* S, int64_t id) {
     if (!r || r->id != id) continue;
     if (!r->done) return FR_ERR_INVALID_ARG;
     if (cudaSetDevice(S->device) != cudaSuccess) return FR_ERR_CUDA;
-    cudaStreamSynchronize(S->stream);
-    r->job.release();
+    // freed after the work queued on the step stream, without waiting
+    r->job.release_async(S->stream);
     delete r;
     r = nullptr;
     return FR_OK;

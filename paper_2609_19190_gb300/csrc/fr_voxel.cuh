@@ -520,8 +520,10 @@ static __device__ void first_order(Win& w, const Arena& A, const FrJob& job,
       f[15] = kNaNf;
     } else {
       f[14] = __fdividef(i128_to_f32(d3) * sqrtf(fn), m2 * sqrtf(m2));
-      f[15] = __fdividef(fn * __fdividef(i128_to_f32(d4), m2), m2) -
-              (job.kurt_excess ? 3.f : 0.f);
+      // N d4 / d2^2 (= m4 / m2^2) minus 3 cancels when the kurtosis is
+      // near 3, so this one quotient is taken in FP64 from the exact sums
+      const double q2 = i128_to_f64(d2);
+      f[15] = (float)((double)N * i128_to_f64(d4) / (q2 * q2) - (job.kurt_excess ? 3.0 : 0.0));
     }
     f[16] = __fdividef(m2, fn * fn * fn);
     f[17] = __fdividef((float)u2, fn * fn);

@@ -90,7 +90,8 @@ def request_bytes(shape, n_voi, n_rows, brick=(8, 4, 4), voxels_per_item=16):
 
 def serve(requests, images, rate, *, seed=0, voxel_budget=65536, hbm_reserve=4 << 30,
           hbm_budget=None, device=0, max_radius=3, keep_outputs=False, tune=None,
-          time_limit=None, drain_dir=None, drain_codec="gzip", drain_workers=2):
+          time_limit=None, drain_dir=None, drain_codec="gzip", drain_workers=2,
+          admit_per_step=6, max_active=256):
     """Run the request stream; returns a dict of statistics (and the outputs
     by request index when keep_outputs).
 
@@ -102,12 +103,17 @@ def serve(requests, images, rate, *, seed=0, voxel_budget=65536, hbm_reserve=4 <
     drain_dir: write each finished request to <drain_dir>/request_<i>.h5
     (fr_h5_write_maps) on host worker threads, off the GPU loop; the maps are
     copied to the host first, so the request's device memory is released at
-    once.  Latencies count up to the device result, not the file."""
+    once.  Latencies count up to the device result, not the file.
+    admit_per_step: requests planned per loop turn while others are on the
+    GPU, so planning never leaves the two steps in flight without a
+    successor for long.  max_active: admitted requests at most (the
+    server's slots); beyond it arrivals wait in the queue, which counts in
+    their latency."""
     import torch
     n = len(requests)
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n)) if rate > 0 else np.zeros(n)
-    srv = Server(device, max_radius=max_radius, tune=tune)
+    srv = Server(device, max_radius=max_radius, max_slots=max_active, tune=tune)
     pending = collections.deque(range(n))
     active = {}
     latency = np.full(n, np.nan)
@@ -145,7 +151,9 @@ def serve(requests, images, rate, *, seed=0, voxel_budget=65536, hbm_reserve=4 <
         if time_limit is not None and now > time_limit:
             break
         # admission: arrived requests, in order, while memory and slots allow
-        while pending and arrivals[pending[0]] <= now:
+        admitted = 0
+        while (pending and arrivals[pending[0]] <= now and len(active) < max_active and
+               (admitted < admit_per_step or not active)):
             i = pending[0]
             rq = requests[i]
             est = request_bytes(rq["shape"], rq["n_voi"], feats)
@@ -165,6 +173,7 @@ def serve(requests, images, rate, *, seed=0, voxel_budget=65536, hbm_reserve=4 <
             in_use += est
             peak_in_use = max(peak_in_use, in_use)
             pending.popleft()
+            admitted += 1
         if active:
             srv.step(voxel_budget)
             steps += 1

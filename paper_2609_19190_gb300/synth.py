@@ -137,6 +137,39 @@ def batch_item(index, base_seed=100):
     return img, mask, radius, bins
 
 
+def batch_small_item(index, base_seed=1000):
+    """One VOI of the many-small-VOIs batch: an ellipsoidal VOI of
+    log-uniform size in [4k, 20k] voxels, random aspect ratio and centre, in
+    one of 16 CT-like 64 x 64 x 64 volumes (index mod 16); radius in {1, 2,
+    3}; bin count in {16, 32, 64}.  One such VOI leaves most of the chip idle
+    in a launch of its own.  Returns (image, mask, radius, bin_count)."""
+    seed = base_seed + index
+    rng = np.random.default_rng(seed)
+    target = float(np.exp(rng.uniform(np.log(4000.0), np.log(20000.0))))
+    aspect = rng.uniform(0.7, 1.3, size=3)
+    scale = (target / (4.0 / 3.0 * np.pi * np.prod(aspect))) ** (1.0 / 3.0)
+    semi = np.minimum(aspect * scale, np.array([24.0, 24.0, 24.0]))
+    radius = int(rng.integers(1, 4))
+    bins = int(rng.choice([16, 32, 64]))
+    centre = tuple(31.5 + rng.uniform(-6.0, 6.0, size=3))
+    shape = (64, 64, 64)
+    img = _ct_shared(shape, base_seed + index % 16)
+    mask = ellipsoid(shape, centre, tuple(semi))
+    return img, mask, radius, bins
+
+
+_CT_SHARED = {}
+
+
+def _ct_shared(shape, seed):
+    """ct_like(shape, seed), computed once per process (callers must not
+    modify it)."""
+    key = (tuple(shape), seed)
+    if key not in _CT_SHARED:
+        _CT_SHARED[key] = ct_like(shape, seed)
+    return _CT_SHARED[key]
+
+
 def paper_tiled(reps=(1, 1, 1), seed=300):
     """A 61 x 55 x 39 (X x Y x Z) MR-like volume (positive smooth intensities)
     with a blob VOI of ~50.6k voxels (38.7 % of the box), repeated reps =
@@ -170,13 +203,18 @@ SERVED_SHAPES = ((32, 64, 64), (64, 64, 64), (64, 128, 128), (128, 128, 128), (1
 
 
 def served_requests(n, seed=200, median=50000.0, sigma=1.0, max_voxels=2000000,
-                    min_voxels=1000):
+                    min_voxels=1000, templates=None):
     """Requests of the served workload: ellipsoidal VOIs of log-normal size
     (median 50k voxels, sigma_ln 1.0, truncated to [1k, 2M]) with a random
     aspect ratio, each in the smallest standard CT-like volume shape that holds
     it; kernel radius uniform in {1, 2, 3}; FBN 64 or FBW 25 HU; all 93 maps.
     Returns a list of dicts with keys shape, mask, radius, disc (parameter
     overrides) and n_voi."""
+    if templates is not None and templates < n:
+        # n arrivals drawn from `templates` distinct requests, in turn (keeps
+        # the host memory of long request streams bounded)
+        base = served_requests(templates, seed, median, sigma, max_voxels, min_voxels)
+        return [base[k % templates] for k in range(n)]
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(n):
