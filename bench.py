@@ -274,9 +274,10 @@ def measure_batched(kind, n_vois, dev, steps=3):
     """Many VOIs, plain against batched.  kind "mixed": 64 CT-like
     128x128x64 VOIs (log-uniform 4k-400k voxels); kind "small": 256 VOIs of
     4k-20k voxels in 64^3 CT-like volumes; r in {1,2,3}, FBN 16/32/64, 93
-    maps.  Plain maps them one plan at a time (4 kernels each: reset,
-    intensity range, discretise/pack, map); batched maps all of them in one
-    persistent launch (the same 4 kernels once, captured in a CUDA graph)
+    maps.  Plain maps them one plan at a time (5 kernels each: reset,
+    intensity range, discretise/pack, voxel order, map); batched maps all of
+    them in one persistent launch (the same 5 kernels once, captured in a
+    CUDA graph)
     with the autotuner's launch shape.  Device time with CUDA events."""
     import torch
     import paper_2609_19190_gb300 as fm
@@ -314,7 +315,7 @@ def measure_batched(kind, n_vois, dev, steps=3):
     return {"value": voxels * 93 / (tb / 1e3), "unit": UNIT, "plain_value": voxels * 93 / (tp / 1e3),
             "vs_plain": tp / tb, "ms_batched": tb, "ms_plain": tp, "n_vois": n_vois,
             "voxels": voxels, "tune": tune, "tune_timings_ms": timings,
-            "kernels": {"batched": 4, "plain": 4 * n_vois},
+            "kernels": {"batched": 5, "plain": 5 * n_vois},
             "workload": desc + ", r in {1,2,3}, FBN 16/32/64, 93 maps; batched = one persistent "
                                "launch in a CUDA graph"}
 
@@ -668,7 +669,7 @@ def run_flashmap(args):
         "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
         "extra_workloads": extra,
         "batched": batched, "served": served, "scalar": scalar, "drain": drain,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 5 * args.steps,
     }
     print(json.dumps(line), flush=True)
 

@@ -30,6 +30,8 @@ cudaError_t fr_scalar_launch(const FrScalarArgs& a, double* user_out, const int1
 cudaError_t fr_launch_prepare(const FrJob* jobs, int njobs, int64_t max_voi,
                               void* const* run_ptrs, uint32_t* queue, int32_t* status,
                               int sms, cudaStream_t s);
+cudaError_t fr_launch_order(const FrJob* jobs, int njobs, int max_segments, int sms,
+                            cudaStream_t s);
 cudaError_t fr_launch_row_count(const uint8_t* mask, int nx, int rows, int32_t* rowcnt,
                                 cudaStream_t s);
 cudaError_t fr_launch_scan(const int32_t* in, int32_t* out, int n, long long* tot,
@@ -241,7 +243,10 @@ struct JobRes {
   int32_t ngc = 0;  // level cap of this job
   uint32_t* packed = nullptr;
   int32_t* voi = nullptr;
-  int32_t* bcols = nullptr;
+  int32_t* bcols = nullptr;      // columns in brick order (plan)
+  int32_t* bcols_run = nullptr;  // the same, reordered within bricks per run
+  int2* bseg = nullptr;          // non-empty brick segments (offset, count)
+  int32_t nbseg = 0;
   FrJobState* state = nullptr;
   std::vector<FrItem> items;  // job field = 0
   size_t bytes = 0;
@@ -252,9 +257,12 @@ struct JobRes {
     cudaFreeAsync(packed, s);
     cudaFreeAsync(voi, s);
     cudaFreeAsync(bcols, s);
+    cudaFreeAsync(bcols_run, s);
+    cudaFreeAsync(bseg, s);
     cudaFreeAsync(state, s);
     packed = nullptr;
-    voi = bcols = nullptr;
+    voi = bcols = bcols_run = nullptr;
+    bseg = nullptr;
     state = nullptr;
   }
 
@@ -262,9 +270,12 @@ struct JobRes {
     cudaFree(packed);
     cudaFree(voi);
     cudaFree(bcols);
+    cudaFree(bcols_run);
+    cudaFree(bseg);
     cudaFree(state);
     packed = nullptr;
-    voi = bcols = nullptr;
+    voi = bcols = bcols_run = nullptr;
+    bseg = nullptr;
     state = nullptr;
   }
 };
@@ -343,6 +354,16 @@ fr_status build_job(const fr_map_params* p, const uint8_t* mask, const fr_tune& 
     FR_TRY(cudaMemcpyAsync(ho.data(), boff, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     FR_TRY(cudaStreamSynchronize(s));
     const int iv = tune.voxels_per_item;
+    std::vector<int2> segs;
+    for (int b = 0; b < nb; ++b)
+      if (hc[b]) segs.push_back(make_int2(ho[b], hc[b]));
+    j.nbseg = (int32_t)segs.size();
+    j.bseg = dev_alloc_on<int2>(segs.size(), &j.bytes, pool, s);
+    FR_TRY(cudaMemcpyAsync(j.bseg, segs.data(), segs.size() * sizeof(int2),
+                           cudaMemcpyHostToDevice, s));
+    j.bcols_run = dev_alloc_on<int32_t>(n, &j.bytes, pool, s);
+    FR_TRY(cudaMemcpyAsync(j.bcols_run, j.bcols, n * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                           s));
     for (int b = 0; b < nb; ++b) {
       if (!hc[b]) continue;
       const int ix = b % nbx, iy = (b / nbx) % nby, iz = b / (nbx * nby);
@@ -401,6 +422,7 @@ struct Engine {
   fr_tune tune{};
   int nw = 0, stages = 0, tile_bytes = 0, smem = 0, grid = 0;
   int64_t max_voi = 0;
+  int max_nbseg = 0;  // brick segments of the largest job (voxel ordering)
   size_t bytes = 0;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t private_stream = nullptr;
@@ -468,6 +490,7 @@ struct Engine {
       for (auto& j : jobs) {
         r_max = std::max(r_max, j.p.kernel_radius);
         max_voi = std::max(max_voi, j.n_voi);
+        max_nbseg = std::max(max_nbseg, (int)j.nbseg);
       }
       arena = fr_make_arena(r_max);
       tile_bytes = 0;
@@ -514,7 +537,11 @@ struct Engine {
         memset((void*)&h, 0, sizeof(FrJob));
         h.packed = j.packed;
         h.voi = j.voi;
-        h.bcols = j.bcols;
+        h.bcols = j.bcols_run;
+        h.bcols_brick = j.bcols;
+        h.bseg = j.bseg;
+        h.nbseg = j.nbseg;
+        h.order = 1;
         h.state = j.state;
         h.n_voi = j.n_voi;
         h.nx = j.p.nx;
@@ -589,6 +616,8 @@ struct Engine {
     cudaError_t e = fr_launch_prepare(jobs_dev, (int)jobs.size(), max_voi, run_ptrs_dev, queue,
                                       status, sms, s);
     if (e != cudaSuccess) return e;
+    if ((e = fr_launch_order(jobs_dev, (int)jobs.size(), max_nbseg, sms, s)) != cudaSuccess)
+      return e;
     // while capturing, external records stay timing records in the graph
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return e;
@@ -868,6 +897,8 @@ fr_status scalar_open(fr_scalar& S, const fr_map_params* p, const uint8_t* mask)
     h.packed = j.packed;
     h.voi = j.voi;
     h.bcols = j.bcols;
+    h.bcols_brick = j.bcols;
+    h.order = 0;  // scalar extraction has no mapping kernel
     h.state = j.state;
     h.n_voi = j.n_voi;
     h.nx = p->nx;
@@ -1159,6 +1190,7 @@ fr_status fr_debug_matrices(fr_plan* plan, const int16_t* image, const int32_t* 
     items[i].n = 1;
   }
   FrJob hj = E.hjobs[0];
+  hj.order = 0;
   FrJob* djob = nullptr;
   FrItem* ditems = nullptr;
   int32_t* dcols = nullptr;
@@ -1394,7 +1426,11 @@ fr_status fr_server_add(fr_server* S, const fr_map_params* p, const uint8_t* mas
     JobRes& j = r->job;
     h.packed = j.packed;
     h.voi = j.voi;
-    h.bcols = j.bcols;
+    h.bcols = j.bcols_run;
+    h.bcols_brick = j.bcols;
+    h.bseg = j.bseg;
+    h.nbseg = j.nbseg;
+    h.order = 1;
     h.state = j.state;
     h.n_voi = j.n_voi;
     h.nx = j.p.nx;
@@ -1460,7 +1496,8 @@ fr_status fr_server_step(fr_server* S, int64_t voxel_budget, int32_t* n_active) 
   for (ServerReq* r : S->slots) {
     if (!r || r->prepared) continue;
     if (fr_launch_prepare(S->jobs_dev + r->slot, 1, r->job.n_voi, S->run_ptrs_dev + 2 * r->slot,
-                          S->prep_queue, S->prep_status, S->sms, S->stream) != cudaSuccess)
+                          S->prep_queue, S->prep_status, S->sms, S->stream) != cudaSuccess ||
+        fr_launch_order(S->jobs_dev + r->slot, 1, r->job.nbseg, S->sms, S->stream) != cudaSuccess)
       return FR_ERR_CUDA;
     r->prepared = true;
   }

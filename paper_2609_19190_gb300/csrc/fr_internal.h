@@ -4,6 +4,7 @@
 #include <cstdint>
 
 #include <cuda.h>
+#include <vector_types.h>
 
 namespace fr {
 
@@ -65,8 +66,17 @@ struct alignas(128) FrJob {
   CUtensorMap tmap;      // 3-D tiled map over `packed` (uint32, [nz][ny][px])
   uint32_t* packed;      // ((raw + 32768) << 8) | level, 0 outside the VOI
   const int32_t* voi;    // linear voxel index per output column
-  const int32_t* bcols;  // output columns ordered by brick
+  const int32_t* bcols;  // output columns the mapping kernel reads, by brick
   FrJobState* state;
+  // Run-time order of the columns inside each brick (fr_order_kernel): by
+  // the number of distinct levels in each voxel's window, so that the
+  // voxels a CTA maps side by side cost alike.  bcols_brick is the plan's
+  // brick order, bseg its non-empty brick segments (offset, count); bcols
+  // is written by the ordering (== bcols_brick when there is none).
+  const int32_t* bcols_brick;
+  const int2* bseg;
+  int32_t nbseg;
+  int32_t order;  // 1: bcols is reordered per run
   int64_t n_voi;
   int32_t nx, ny, nz, px;
   int32_t r, delta;

@@ -105,6 +105,75 @@ __global__ void fr_pack_kernel(const FrJob* jobs, void* const* run_ptrs) {
   }
 }
 
+// ------------------------------------------------------------------ voxel order
+// Distinct gray levels in the window of the VOI voxel at linear index lin
+// (levels taken mod 64, so the count is exact up to 64 levels), from the
+// packed volume (level 0 = outside the VOI).
+__device__ int fr_window_levels(const FrJob& job, int lin) {
+  const int x = lin % job.nx, y = (lin / job.nx) % job.ny, z = lin / (job.nx * job.ny);
+  const int r = job.r;
+  const int x0 = max(0, x - r), x1 = min(job.nx - 1, x + r);
+  const int y0 = max(0, y - r), y1 = min(job.ny - 1, y + r);
+  const int z0 = max(0, z - r), z1 = min(job.nz - 1, z + r);
+  unsigned long long set = 0ull;
+  for (int zz = z0; zz <= z1; ++zz)
+    for (int yy = y0; yy <= y1; ++yy) {
+      const uint32_t* row = job.packed + ((size_t)zz * job.ny + yy) * job.px;
+      for (int xx = x0; xx <= x1; ++xx) {
+        const uint32_t g = row[xx] & 0xFFu;
+        if (g) set |= 1ull << ((g - 1u) & 63u);
+      }
+    }
+  return __popcll(set);
+}
+
+// Columns of every brick segment of every job, reordered by the window's
+// level count (counting sort, one warp per segment): the voxels of one work
+// item then cost alike and take the same code paths, so the CTA's warps
+// wait less at the family barriers.  The maps do not depend on the order.
+// Grid (blocks, jobs); segments longer than kOrderMax keep the plan order.
+constexpr int kOrderWarps = 8;
+constexpr int kOrderMax = 1024;
+__global__ void __launch_bounds__(32 * kOrderWarps) fr_order_kernel(const FrJob* jobs) {
+  __shared__ uint8_t s_m[kOrderWarps][kOrderMax];
+  __shared__ int s_hist[kOrderWarps][66];
+  const FrJob& job = jobs[blockIdx.y];
+  if (!job.order || job.state->status != 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t* out = const_cast<int32_t*>(job.bcols);
+  for (int seg = blockIdx.x * kOrderWarps + warp; seg < job.nbseg;
+       seg += gridDim.x * kOrderWarps) {
+    const int2 sg = job.bseg[seg];
+    const int off = sg.x, cnt = sg.y;
+    if (cnt > kOrderMax) {
+      for (int i = lane; i < cnt; i += 32) out[off + i] = job.bcols_brick[off + i];
+      continue;
+    }
+    for (int b = lane; b < 66; b += 32) s_hist[warp][b] = 0;
+    __syncwarp();
+    for (int i = lane; i < cnt; i += 32) {
+      const int m = fr_window_levels(job, job.voi[job.bcols_brick[off + i]]);
+      s_m[warp][i] = (uint8_t)m;
+      atomicAdd(&s_hist[warp][m + 1], 1);
+    }
+    __syncwarp();
+    if (lane == 0) {  // exclusive starts of the 65 counts
+      int acc = 0;
+      for (int b = 0; b < 66; ++b) {
+        const int c = s_hist[warp][b];
+        s_hist[warp][b] = acc;
+        acc += c;
+      }
+    }
+    __syncwarp();
+    for (int i = lane; i < cnt; i += 32) {
+      const int pos = atomicAdd(&s_hist[warp][s_m[warp][i] + 1], 1);
+      out[off + pos] = job.bcols_brick[off + i];
+    }
+    __syncwarp();
+  }
+}
+
 // ------------------------------------------------------------------ plan
 // Mask voxels per row (z, y): one warp per row.
 __global__ void fr_row_count_kernel(const uint8_t* mask, int nx, int rows,
@@ -244,6 +313,14 @@ cudaError_t fr_launch_prepare(const FrJob* jobs, int njobs, int64_t max_voi,
   dim3 grid(per_job, njobs);
   fr_minmax_kernel<<<grid, 256, 0, s>>>(jobs, run_ptrs);
   fr_pack_kernel<<<grid, 256, 0, s>>>(jobs, run_ptrs);
+  return cudaGetLastError();
+}
+
+cudaError_t fr_launch_order(const FrJob* jobs, int njobs, int max_segments, int sms,
+                            cudaStream_t s) {
+  if (max_segments < 1) return cudaSuccess;
+  const int blocks = fr_grid_for(max_segments, kOrderWarps, 4 * sms);
+  fr_order_kernel<<<dim3(blocks, njobs), 32 * kOrderWarps, 0, s>>>(jobs);
   return cudaGetLastError();
 }
 

@@ -724,6 +724,100 @@ __device__ __forceinline__ int sturm_count(const float (&d)[N], const float (&e2
 constexpr int kMccRounds1 = 22;
 constexpr int kMccRounds2 = 14;
 
+// Largest |eigenvalue| of the symmetric n x n matrix (n <= N <= 32, row
+// stride kMCap) at src, by one warp with the matrix in registers: lane i
+// holds row i (zero beyond n; zero rows and columns only add the eigenvalue
+// 0, which every deflated S - u u^T already has).  Householder
+// tridiagonalisation with the step loop unrolled, so every row element is a
+// register: per step the column's tail norm is one warp sum, p = A v takes
+// v_j from lane j by shuffle, and the rank-2 update A -= 2 (v w^T + w v^T)
+// takes w_j the same way; rows above the step are never read again, so they
+// are left as they are.  Then Sturm-count multisection of [0, B] (B the
+// Gershgorin bound) over 32 shifts per round, one per lane, counting the
+// eigenvalues of either sign beyond the shift.  Every lane returns the same
+// value (warp sums by xor butterflies give every lane identical totals).
+template <int N>
+__device__ float pool_rho_regs(const float* __restrict__ src, int n) {
+  static_assert(N <= 32, "one row per lane");
+  const int lane = lane_id();
+  float a[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) a[j] = (lane < n && j < n) ? src[lane * kMCap + j] : 0.f;
+  float dk = 0.f, ek = 0.f;  // lane k ends with d_k and e_k (the (k, k+1) entry)
+#pragma unroll
+  for (int k = 0; k + 2 < N; ++k) {
+    const float x = lane > k ? a[k] : 0.f;
+    const float x1 = __shfl_sync(kFull, a[k], k + 1);
+    float t1[1] = {lane > k + 1 ? x * x : 0.f};
+    warp_sum_f32x<1>(t1);
+    const float tail = t1[0];
+    if (lane == k) dk = a[k];
+    if (tail == 0.f) {  // the column is already reduced (the same on every lane)
+      if (lane == k) ek = x1;
+      continue;
+    }
+    const float alpha = -copysignf(sqrtf(tail + x1 * x1), x1);
+    const float inv = rsqrtf(2.f * (alpha * alpha - alpha * x1));
+    const float v = lane > k ? (lane == k + 1 ? x1 - alpha : x) * inv : 0.f;
+    float vb[N];
+    float p = 0.f;
+#pragma unroll
+    for (int j = k + 1; j < N; ++j) {
+      vb[j] = __shfl_sync(kFull, v, j);
+      p = fmaf(a[j], vb[j], p);
+    }
+    float kp[1] = {v * p};
+    warp_sum_f32x<1>(kp);
+    const float w = p - kp[0] * v;
+#pragma unroll
+    for (int j = k + 1; j < N; ++j) {
+      const float wj = __shfl_sync(kFull, w, j);
+      a[j] -= 2.f * (v * wj + w * vb[j]);
+    }
+    if (lane == k) ek = alpha;
+  }
+  if (lane == N - 2) {
+    dk = a[N - 2];
+    ek = a[N - 1];
+  }
+  if (lane == N - 1) dk = a[N - 1];
+  // the tridiagonal (d, e^2) in every lane
+  float d[N], e2[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    d[i] = __shfl_sync(kFull, dk, i);
+    const float e = __shfl_sync(kFull, ek, i);
+    e2[i] = e * e;
+  }
+  float bnd = 0.f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float r = fabsf(d[i]);
+    if (i > 0) r += sqrtf(e2[i - 1]);
+    if (i < N - 1) r += sqrtf(e2[i]);
+    bnd = fmaxf(bnd, r);
+  }
+  float lo = 0.f, hi = bnd * 1.0001f + 1e-20f;
+  for (int round = 0; round < 6; ++round) {
+    const float step = (hi - lo) * (1.f / 33.f);
+    const float sig = lo + step * (float)(lane + 1);
+    // eigenvalues above sig plus eigenvalues below -sig
+    const int cnt = (N - sturm_count<N>(d, e2, 1.f, sig)) + sturm_count<N>(d, e2, 1.f, -sig);
+    const unsigned msk = __ballot_sync(kFull, cnt > 0);
+    if (msk == 0u) {
+      hi = lo + step;
+    } else {
+      const int L = 31 - __clz(msk);
+      const float nlo = lo + step * (float)(L + 1);
+      const float nhi = (L == 31) ? hi : lo + step * (float)(L + 2);
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  return 0.5f * (lo + hi);
+}
+
+
 // Largest |eigenvalue| of a symmetric N x N matrix read from a packed upper
 // triangle in the kCapL x kCapL layout, by one thread with every value in
 // registers.  Rows and columns beyond the matrix hold zeros: they only add
@@ -1526,17 +1620,17 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
 }
 
 // One warp's share of the CTA pool: take listed tasks until none is left;
-// each copies the owner's matrix into this warp's shared-memory region, solves
-// it there, clears it, and stores the radius in the owner's results.  Every
-// consumer warp calls this between two CTA barriers (the list is complete).
+// each loads the owner's matrix into the warp's registers (a row per lane),
+// solves it there (pool_rho_regs) and stores the radius in the owner's
+// results.  Every consumer warp calls this between two CTA barriers (the
+// list is complete).
 static __device__ void fb_pool_work(const FbPool& P, const FrMapArgs& args, int W,
                                     unsigned char* arenas, int arena_bytes, int arena_off_big,
                                     char* my_big) {
   const int lane = lane_id();
   const BigLayout L = fr_big_layout(kMCap, kBinCap, W);
   const int count = *(volatile int*)P.count;
-  float* S = (float*)my_big;  // this warp's count region (zero on entry and exit)
-  float* vv = (float*)(my_big + L.vec);
+  (void)my_big;
   while (true) {
     int t = 0;
     if (lane == 0) t = atomicAdd(P.next, 1);
@@ -1546,17 +1640,8 @@ static __device__ void fb_pool_work(const FbPool& P, const FrMapArgs& args, int 
     const int owner = task >> 16, d = (task >> 8) & 0xFF, n = task & 0xFF;
     const float* src = args.fb + ((size_t)blockIdx.x * args.consumer_warps + owner) * args.fb_stride +
                        (size_t)d * kMCap * kMCap;
-    for (int e = lane; e < n * n; e += 32) {
-      const int a = e / n, b = e - a * n;
-      S[a * kMCap + b] = src[a * kMCap + b];
-    }
-    __syncwarp();
-    const float rho = spectral_radius(S, n, kMCap, vv, vv + kMCap, vv + 2 * kMCap, vv + 3 * kMCap);
-    __syncwarp();
-    for (int e = lane; e < n * n; e += 32) {
-      const int a = e / n, b = e - a * n;
-      S[a * kMCap + b] = 0.f;
-    }
+    // tasks have more than kCapL levels: 13..16 or 17..kMCap rows
+    const float rho = n <= 16 ? pool_rho_regs<16>(src, n) : pool_rho_regs<kMCap>(src, n);
     if (lane == 0) {
       float* mres = (float*)(arenas + (size_t)owner * arena_bytes + arena_off_big + L.mres);
       mres[d] = rho;
