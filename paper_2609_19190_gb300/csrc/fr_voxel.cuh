@@ -520,10 +520,20 @@ static __device__ void first_order(Win& w, const Arena& A, const FrJob& job,
       f[15] = kNaNf;
     } else {
       f[14] = __fdividef(i128_to_f32(d3) * sqrtf(fn), m2 * sqrtf(m2));
-      // N d4 / d2^2 (= m4 / m2^2) minus 3 cancels when the kurtosis is
-      // near 3, so this one quotient is taken in FP64 from the exact sums
-      const double q2 = i128_to_f64(d2);
-      f[15] = (float)((double)N * i128_to_f64(d4) / (q2 * q2) - (job.kurt_excess ? 3.0 : 0.0));
+      // m4 / m2^2 = N d4 / d2^2, and "minus 3" cancels when the kurtosis is
+      // near 3: the excess is taken from the exact numerator N d4 - 3 d2^2
+      // (int128: d2 < 2^56 keeps d2^2 < 2^112 and N d4 <= N d2^2 < 2^124),
+      // else from the same quotient in FP64
+      const float fd2 = i128_to_f32(d2);
+      float kex;
+      if ((d2 >> 56) == 0 && N <= 4096) {
+        const __int128 knum = (__int128)N * d4 - 3 * d2 * d2;
+        kex = __fdividef(i128_to_f32(knum), fd2 * fd2);
+      } else {
+        const double q2 = i128_to_f64(d2);
+        kex = (float)((double)N * i128_to_f64(d4) / (q2 * q2) - 3.0);
+      }
+      f[15] = job.kurt_excess ? kex : __fdividef(fn * __fdividef(i128_to_f32(d4), m2), m2);
     }
     f[16] = __fdividef(m2, fn * fn * fn);
     f[17] = __fdividef((float)u2, fn * fn);
