@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="flashmap", choices=["flashmap", "reference"])
     ap.add_argument("--workload", default="ct_large",
-                    choices=["ct_plain", "tiny", "ct_large", "paper_tiled"])
+                    choices=["ct_plain", "tiny", "ct_large", "ct_large_slab16", "paper_tiled"])
     ap.add_argument("--extra-workloads", default="ct_plain",
                     help="comma-separated workloads timed as extra legs (kernel only)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -90,6 +90,16 @@ def workload(name):
         kw = dict(disc_mode=0, bin_count=64, kernel_radius=3, glcm_distance=1)
         desc = ("CT-like 256x256x128 int16, union of 3 ellipsoids, FBN 64, r=3 (7^3), "
                 "delta=1, 93 maps")
+    elif name == "ct_large_slab16":
+        # the same volume, the VOI voxels of slices 56..71 only (492,804
+        # voxels): a capture-sized case of the same kernel paths for ncu
+        img, mask = synth.ct_large(seed=3)
+        mask = mask.copy()
+        mask[:56] = 0
+        mask[72:] = 0
+        kw = dict(disc_mode=0, bin_count=64, kernel_radius=3, glcm_distance=1)
+        desc = ("CT-like 256x256x128 int16, the union-of-3-ellipsoids VOI cut to slices "
+                "56..71, FBN 64, r=3 (7^3), delta=1, 93 maps")
     else:
         img, mask = synth.paper_tiled(reps=(2, 2, 2))
         kw = dict(disc_mode=1, bin_width=25.0, kernel_radius=1, glcm_distance=1)

@@ -334,6 +334,11 @@ fr_status fr_measure_alu_peak(int32_t device, double* int32_add_per_s, double* i
  *   `device` becomes the calling thread's current device.  The first call on
  *   a device looks up the scratch's device address (once per device, with
  *   that device current): make that first call before any stream capture.
+ *   The address is kept for the life of the process: after a
+ *   cudaDeviceReset of that device it is stale, so the entry point must not
+ *   be used again in that process.  An error left pending by earlier CUDA
+ *   work of the thread is returned (and cleared) as FR_ERR_CUDA before
+ *   anything is launched.
  *   Every call shares the scratch and overwrites every word of it that it
  *   reads; calls that overlap on the GPU (other streams, other threads) race.
  *   The call synchronises stream s once, to read the count; the list itself

@@ -397,11 +397,14 @@ def fr_voxel_list_noalloc(mask, stream=None):
     torch = _torch()
     assert mask.is_cuda and mask.dtype == torch.uint8 and mask.is_contiguous()
     nz, ny, nx = mask.shape
-    voi = torch.empty(mask.numel(), dtype=torch.int32, device=mask.device)
-    n = C.c_int64()
-    check("fr_voxel_list_noalloc", _lib.load().fr_voxel_list_noalloc(
-        C.c_void_p(mask.data_ptr()), nx, ny, nz, C.c_void_p(voi.data_ptr()), voi.numel(),
-        C.byref(n), mask.device.index or 0, _stream_ptr(stream)))
+    with torch.cuda.device(mask.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(mask.device)
+        voi = torch.empty(mask.numel(), dtype=torch.int32, device=mask.device)
+        n = C.c_int64()
+        check("fr_voxel_list_noalloc", _lib.load().fr_voxel_list_noalloc(
+            C.c_void_p(mask.data_ptr()), nx, ny, nz, C.c_void_p(voi.data_ptr()), voi.numel(),
+            C.byref(n), mask.device.index or 0, C.c_void_p(stream.cuda_stream)))
     return voi[:n.value]
 
 

@@ -525,7 +525,7 @@ struct Engine {
       } else {
         slab_stride = 0;
       }
-      fb_stride = (int64_t)kNumDirs * kMCap * kMCap;
+      fb_stride = (int64_t)kNumDirs * kFbDir;
       fb = dev_alloc<float>((size_t)grid * nw * fb_stride, &bytes);
       // device job table with tensor maps
       PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
@@ -1375,7 +1375,7 @@ fr_status fr_server_create(int32_t device, int32_t max_radius, int32_t max_slots
     S->slab_stride = fr_align(fr_big_layout(S->slab_ngc, S->slab_ngc, S->arena.w_max).bytes, 256);
     S->slab = dev_alloc<char>((size_t)S->grid * S->nw * S->slab_stride, &S->bytes);
     FR_TRY(cudaMemsetAsync(S->slab, 0, (size_t)S->grid * S->nw * S->slab_stride, S->stream));
-    S->fb_stride = (int64_t)kNumDirs * kMCap * kMCap;
+    S->fb_stride = (int64_t)kNumDirs * kFbDir;
     S->fb = dev_alloc<float>((size_t)S->grid * S->nw * S->fb_stride, &S->bytes);
     S->jobs_dev = dev_alloc<FrJob>(max_slots, &S->bytes);
     S->run_ptrs_dev = dev_alloc<void*>(2 * (size_t)max_slots, &S->bytes);

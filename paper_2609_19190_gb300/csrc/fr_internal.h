@@ -40,8 +40,12 @@ constexpr int kMaxConsumerWarps = 16;
 constexpr int kPadMaxSide = 7;
 constexpr int kPadCells = (kPadMaxSide + 2) * (kPadMaxSide + 2) * (kPadMaxSide + 2);
 constexpr int kMaxStages = 4;
-// CTA pool of many-level MCC solves: at most one per direction per warp
+// CTA pool of many-level MCC solves: at most one per direction per warp;
+// each direction's S - u u^T is a dense m x m block (row stride m, so the
+// lines a solve touches are contiguous) in the warp's global scratch
+// (kFbDir floats per direction)
 constexpr int kFbTasks = kMaxConsumerWarps * kNumDirs;
+constexpr int kFbDir = kMCap * kMCap;
 
 // Feature families (bits of FrJob::families).
 enum : uint32_t {
@@ -133,7 +137,7 @@ struct FrMapArgs {
   int32_t slab_ngc;    // level cap the slab is laid out for
   FrArena arena;
   float* fb;           // per-warp matrices of many-level MCC solves (kNumDirs x
-  int64_t fb_stride;   // kMCap^2 floats each) handed to the CTA's pool; null: inline
+  int64_t fb_stride;   // kFbDir floats each) handed to the CTA's pool; null: inline
   int32_t* dbg;        // debug records (DUMP kernel only)
   int64_t dbg_stride;  // int32 per record
   int64_t timeout_ns;  // bound of every device wait

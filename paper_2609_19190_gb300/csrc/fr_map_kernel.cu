@@ -220,7 +220,9 @@ __device__ void map_voxel(const FrMapArgs& args, const FrJob& job,
     float* out = (float*)args.run_ptrs[2 * item.job + 1];
     for (int f = lane; f < kNumFeatures; f += 32) {
       const int row = job.row_of[f];
-      if (row >= 0) out[(size_t)row * job.n_voi + col] = A.fv[f];
+      // maps are written once and never read here: streaming stores keep
+      // them from evicting the MCC scratch from L2
+      if (row >= 0) __stcs(&out[(size_t)row * job.n_voi + col], A.fv[f]);
     }
     __syncwarp();
   }

@@ -66,6 +66,9 @@ extern "C" fr_status fr_voxel_list_noalloc(const uint8_t* mask, int32_t nx, int3
       device >= kMaxDevices)
     return FR_ERR_UNSUPPORTED;
   if (cudaSetDevice(device) != cudaSuccess) return FR_ERR_CUDA;
+  // an error left pending by earlier work of this thread is reported (and
+  // cleared) here, so that a failure below belongs to this call's launches
+  if (cudaGetLastError() != cudaSuccess) return FR_ERR_CUDA;
   unsigned char* base = nullptr;
   fr_status st = scratch_for_device(device, &base);
   if (st != FR_OK) return st;

@@ -734,8 +734,8 @@ __device__ __forceinline__ int sturm_count(const float (&d)[N], const float (&e2
 constexpr int kMccRounds1 = 22;
 constexpr int kMccRounds2 = 14;
 
-// Largest |eigenvalue| of the symmetric n x n matrix (n <= N <= 32, row
-// stride kMCap) at src, by one warp with the matrix in registers: lane i
+// Largest |eigenvalue| of the symmetric n x n matrix (n <= N <= 32, dense,
+// row stride n) at src, by one warp with the matrix in registers: lane i
 // holds row i (zero beyond n; zero rows and columns only add the eigenvalue
 // 0, which every deflated S - u u^T already has).  Householder
 // tridiagonalisation with the step loop unrolled, so every row element is a
@@ -752,7 +752,8 @@ __device__ float pool_rho_regs(const float* __restrict__ src, int n) {
   const int lane = lane_id();
   float a[N];
 #pragma unroll
-  for (int j = 0; j < N; ++j) a[j] = (lane < n && j < n) ? src[lane * kMCap + j] : 0.f;
+  for (int j = 0; j < N; ++j)
+    a[j] = (lane < n && j < n) ? src[lane * n + j] : 0.f;
   float dk = 0.f, ek = 0.f;  // lane k ends with d_k and e_k (the (k, k+1) entry)
 #pragma unroll
   for (int k = 0; k + 2 < N; ++k) {
@@ -1351,12 +1352,12 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
     // warp-cooperative solve into the (zero) count region
     const bool fill_s = S > 0 && want_mcc && present > kCapL;
     const bool pooled = pool != nullptr && want_mcc && present > kCapL;
-    float* Sm = pooled ? pool->scratch + (size_t)ds * kMCap * kMCap : (float*)cnt;
+    // pooled: dense m x m (row stride m, contiguous) in the warp's global
+    // scratch; else dense (stride mc) in place of the counts
+    float* Sm = pooled ? pool->scratch + (size_t)ds * kFbDir : (float*)cnt;
+    const int ms = pooled ? m : mc;
     if (fill_s && pooled)  // the pair lanes write only present pairs
-      for (int t = lane; t < mm2; t += 32) {
-        const int a = (int)mm.div((unsigned)t);
-        Sm[a * mc + (t - a * m)] = 0.f;
-      }
+      for (int t = lane; t < mm2; t += 32) Sm[t] = 0.f;
     float* P = slots + ds * kSlot;
     const float invT = __fdividef(1.f, fT);
     if (slot)
@@ -1406,8 +1407,8 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
           const float v = (float)(-cc) * rsqrtf((float)ca * (float)cb) * invT;
           if (slot) P[pk(kCapL, pa, pbk)] = v;
           if (fill_s) {
-            Sm[a * mc + b] = v;
-            Sm[b * mc + a] = v;
+            Sm[a * ms + b] = v;
+            Sm[b * ms + a] = v;
           }
           continue;
         }
@@ -1425,9 +1426,9 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
         const float v = (float)(ct - cc) * rsqrtf((float)ca * (float)cb) * invT;
         if (slot) P[pk(kCapL, pa, pbk)] = v;
         if (fill_s) {
-          Sm[a * mc + b] = v;
-          Sm[b * mc + a] = v;
-        }
+            Sm[a * ms + b] = v;
+            Sm[b * ms + a] = v;
+          }
         atomicAdd(&sbin[i + j - 2 * w.lev0], 2 * n);
         atomicAdd(&dbin[j - i], 2 * n);
         if (dbg_glcm) {
@@ -1516,8 +1517,8 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
             const long long num = (long long)C * T - (long long)ca * cb;
             v = __fdividef((float)num * rsqrtf((float)ca * (float)cb), fT);
           }
-          Sm[a * mc + b] = v;
-          Sm[b * mc + a] = v;
+          Sm[a * ms + b] = v;
+          Sm[b * ms + a] = v;
         }
         __syncwarp();
         if (pooled) {
@@ -1649,7 +1650,7 @@ static __device__ void fb_pool_work(const FbPool& P, const FrMapArgs& args, int 
     const int task = P.tasks[t];
     const int owner = task >> 16, d = (task >> 8) & 0xFF, n = task & 0xFF;
     const float* src = args.fb + ((size_t)blockIdx.x * args.consumer_warps + owner) * args.fb_stride +
-                       (size_t)d * kMCap * kMCap;
+                       (size_t)d * kFbDir;
     // tasks have more than kCapL levels: 13..16 or 17..kMCap rows
     const float rho = n <= 16 ? pool_rho_regs<16>(src, n) : pool_rho_regs<kMCap>(src, n);
     if (lane == 0) {
@@ -1881,11 +1882,11 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
       const bool many = want_mcc && present > kCapL;
       const bool slot = want_mcc && present >= 2 && !many;
       float* P = slots + d * kSlot;
-      float* Sm = many ? pool->scratch + (size_t)d * kMCap * kMCap : nullptr;
+      float* Sm = many ? pool->scratch + (size_t)d * kFbDir : nullptr;  // dense, row stride m
       if (slot)
         for (int t = h; t < kSlot; t += 2) P[t] = 0.f;
       if (many)
-        for (int t = h; t < m * m; t += 2) Sm[(t / m) * kMCap + t % m] = 0.f;
+        for (int t = h; t < m * m; t += 2) Sm[t] = 0.f;
       if (!h) {
         mn[d] = slot ? present : 0;
         if (!slot) mres[d] = kNaNf;
@@ -1933,8 +1934,8 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
             const float v = (float)(-cc) * rsqrtf((float)ca * (float)cb) * invT;
             if (slot) P[pk(kCapL, pa, pb)] = v;
             if (many) {
-              Sm[a * kMCap + b] = v;
-              Sm[b * kMCap + a] = v;
+              Sm[a * m + b] = v;
+              Sm[b * m + a] = v;
             }
             continue;
           }
@@ -1952,8 +1953,8 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
             const float v = (float)(ct - cc) * rsqrtf((float)ca * (float)cb) * invT;
             if (slot) P[pk(kCapL, pa, pb)] = v;
             if (many) {
-              Sm[a * kMCap + b] = v;
-              Sm[b * kMCap + a] = v;
+              Sm[a * m + b] = v;
+              Sm[b * m + a] = v;
             }
           }
           if (dbg_glcm) {

@@ -67,3 +67,36 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     rc, n = _call(L, mask, 4, 4, 4, voi, 10)
     assert rc == 1 and n == 64
     assert bool((voi == -1).all())
+
+
+def test_noalloc_allocates_nothing_and_handles_edges():
+    # after a first call (which looks up the static scratch once), further
+    # calls leave the device's free memory unchanged: the output is the
+    # caller's and the scratch is the static array
+    import torch
+
+    import paper_2609_19190_gb300 as fm
+    from paper_2609_19190_gb300 import _lib
+    L = _lib.load()
+    mask = torch.from_numpy(synth.tiny(seed=1)[1]).cuda()
+    nz, ny, nx = mask.shape
+    voi = torch.full((mask.numel(),), -1, dtype=torch.int32, device="cuda")
+    rc, n = _call(L, mask, nx, ny, nz, voi, voi.numel())
+    assert rc == 0
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        rc, n2 = _call(L, mask, nx, ny, nz, voi, voi.numel())
+        assert rc == 0 and n2 == n
+    assert torch.cuda.mem_get_info()[0] == free0
+    # a capacity of exactly n is enough
+    exact = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    rc, n3 = _call(L, mask, nx, ny, nz, exact, n)
+    assert rc == 0 and n3 == n and torch.equal(exact, voi[:n])
+    # an empty mask: zero voxels, the output untouched
+    empty = torch.zeros((5, 6, 7), dtype=torch.uint8, device="cuda")
+    out = torch.full((8,), -1, dtype=torch.int32, device="cuda")
+    rc, n0 = _call(L, empty, 7, 6, 5, out, out.numel())
+    assert rc == 0 and n0 == 0 and bool((out == -1).all())
+    # the Python wrapper gives the same list
+    assert torch.equal(fm.fr_voxel_list_noalloc(mask), voi[:n])
