@@ -180,6 +180,45 @@ __device__ __forceinline__ float lane_quot(float num, float den) {
   return den == 0.f ? kNaNf : __fdividef(num, den);
 }
 
+// ------------------------------------------------------------------ float pairs
+// A float pair hi + lo carries about 48 significant bits in fp32 arithmetic
+// (GB300's FP64 issues at a small fraction of its fp32 rate).
+// f integer-valued (any float of magnitude >= 2^24 is) -> int128, exactly.
+__device__ __forceinline__ __int128 f32_to_i128(float f) {
+  const unsigned u = __float_as_uint(f);
+  const int be = (int)((u >> 23) & 0xFFu);
+  if (be == 0) return 0;
+  const unsigned mant = (u & 0x7FFFFFu) | 0x800000u;
+  const int e = be - 150;  // f = mant * 2^e
+  const __int128 v = e >= 0 ? ((__int128)mant << e) : (__int128)(mant >> (-e));
+  return (u >> 31) ? -v : v;
+}
+// x = hi + lo: hi the nearest float, lo the float nearest the exact rest
+__device__ __forceinline__ float2 i128_to_ff(__int128 x) {
+  const float hi = i128_to_f32(x);
+  return make_float2(hi, i128_to_f32(x - f32_to_i128(hi)));
+}
+// x / t^4 for an integer 1 <= t < 4096: t^4 = dh + dl exactly; q = RN(x.hi /
+// dh) leaves the exact residual x.hi - q dh (one FMA), so the pair's quotient
+// is q + (residual + x.lo - q dl) / dh
+__device__ __forceinline__ float2 ff_div_t4(float2 x, int t) {
+  const float t2 = (float)(t * t);
+  const float dh = __fmul_rn(t2, t2), dl = fmaf(t2, t2, -dh);
+  const float q = __fdiv_rn(x.x, dh);
+  const float r = fmaf(-q, dh, x.x);
+  const float e = fmaf(-q, dl, __fadd_rn(r, x.y));
+  return make_float2(q, __fdividef(e, dh));
+}
+// (a.hi + a.lo) + (b.hi + b.lo) with the rounding error of the high parts
+// kept exactly (TwoSum, additions only); commutative bit for bit
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x), v = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fadd_rn(__fsub_rn(a.x, __fsub_rn(s, v)), __fsub_rn(b.x, v)),
+                            __fadd_rn(a.y, b.y));
+  const float hi = __fadd_rn(s, e);
+  return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+
 // ------------------------------------------------------------------ sorting
 // Compare-exchange of keys i and i ^ j held in one lane's registers.
 __device__ __forceinline__ void cx_reg(uint32_t& lo_slot, uint32_t& hi_slot, bool up) {
@@ -1128,14 +1167,14 @@ struct FbPool {
 };
 
 // After the 13 directions: the deferred MCC solves (one lane per direction),
-// the direction means, and ClusterShade's FP64 mean.
+// the direction means, and ClusterShade's mean (in float pairs).
 static __device__ void glcm_finish(const Arena& A, const FrJob& job) {
   const int lane = lane_id();
   const bool want_mcc = (job.families & kFamMCC) != 0;
   int* mn = (int*)(A.big + A.L.mn);
   float* mres = (float*)(A.big + A.L.mres);
   float* slots = (float*)(A.big + A.L.slots);
-  double* csn = (double*)(A.big + A.L.csn);
+  float2* csn = (float2*)(A.big + A.L.csn);
   int* cst = (int*)(A.big + A.L.cst);
   __syncwarp();
   if (want_mcc) {
@@ -1176,15 +1215,18 @@ static __device__ void glcm_finish(const Arena& A, const FrJob& job) {
   {
     __syncwarp();
     const int t = lane < kNumDirs ? cst[lane] : 0;
-    double v = 0.0;
-    if (t > 0) {
-      const double dt = (double)t;
-      v = csn[lane] / (dt * dt * dt * dt);
-    }
+    float2 v = make_float2(0.f, 0.f);
+    if (t > 0) v = ff_div_t4(csn[lane], t);
     const int n = __popc(__ballot_sync(kFull, t > 0));
 #pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if (lane == 3 && n) A.fv[18 + 3] = (float)(v / (double)n);
+    for (int o = 16; o; o >>= 1) {
+      const float2 w = make_float2(__shfl_xor_sync(kFull, v.x, o), __shfl_xor_sync(kFull, v.y, o));
+      v = ff_add(v, w);
+    }
+    if (lane == 3 && n) {
+      const float fn = (float)n, q = __fdiv_rn(v.x, fn);
+      A.fv[18 + 3] = q + __fdividef(__fadd_rn(fmaf(-q, fn, v.x), v.y), fn);
+    }
     if (lane < kNumDirs) cst[lane] = 0;  // leave the big region zero
     __syncwarp();
   }
@@ -1227,9 +1269,10 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
   acc_reset(A);
   // ClusterShade: per-direction values of either sign (hundreds, for
   // near-symmetric windows) can average to ~1e-2, below what fp32 keeps
-  // after rounding each; their exact numerators (FP64) and totals are kept
-  // per direction and summed in FP64 after the loop
-  double* csn = (double*)(A.big + A.L.csn);
+  // after rounding each; their exact numerators (as float pairs, about 48
+  // bits) and totals are kept per direction and averaged in float pairs
+  // after the loop
+  float2* csn = (float2*)(A.big + A.L.csn);
   int* cst = (int*)(A.big + A.L.cst);
   if (lane < kNumDirs) cst[lane] = 0;
   constexpr int SS = S > 0 ? S : 1;
@@ -1605,7 +1648,7 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
     if (lane == 3) {
       num = i128_to_f32(ce3);
       den = fT * fT * fT * fT;
-      csn[ds] = i128_to_f64(ce3);
+      csn[ds] = i128_to_ff(ce3);
       cst[ds] = T;
     }
     if (lane == 4) { num = fa; den = fT * fT * fT; }
@@ -1722,7 +1765,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
   int* mn = (int*)(A.big + A.L.mn);
   float* mres = (float*)(A.big + A.L.mres);
   float* slots = (float*)(A.big + A.L.slots);
-  double* csn = (double*)(A.big + A.L.csn);
+  float2* csn = (float2*)(A.big + A.L.csn);
   int* cst = (int*)(A.big + A.L.cst);
   acc_reset(A);
   for (int q = lane; q < 48; q += 32) ((unsigned*)cntk)[q] = 0u;
@@ -2045,7 +2088,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
         }
         fval[2] = __fdividef(ce4, fT * fT * fT * fT * fT);
         fval[3] = __fdividef(i128_to_f32(ce3), fT * fT * fT * fT);
-        csn[d] = i128_to_f64(ce3);
+        csn[d] = i128_to_ff(ce3);
         cst[d] = T;
         fval[4] = __fdividef(ce2, fT * fT * fT);
         fval[20] = __fdividef((float)sk, fT);
