@@ -43,7 +43,17 @@ ALU_LANES_PER_SM = 128  # fp32/int32 lanes per Blackwell SM
 # them stale and the bench reports null): DRAM bytes (read + write) per
 # launch, issue-slot utilisation and shared-memory pipe utilisation (% of
 # peak), as summarised under profiles/.
-NCU_COUNTERS = {}
+NCU_COUNTERS = {
+    # profiles/: 770 B of DRAM traffic per VOI voxel on the 492,804-voxel band
+    # of the same volume (32.9 MB read + 346.8 MB written), scaled by voxels
+    # to the 2,014,083-voxel launch; issue slots and shared-memory pipe from
+    # the band's full capture
+    ("ct_large", "e4cb427f0f524ac6690cd6925da5c55f6c3c3850060fb8dd72c734ea8b19afb5"):
+        {"traffic": 1551889099, "traffic_basis": "band of 492,804 voxels, scaled by voxels",
+         "issue_active_pct": 47.9, "shared_pipe_pct": 17.4},
+    ("ct_large_slab16", "e4cb427f0f524ac6690cd6925da5c55f6c3c3850060fb8dd72c734ea8b19afb5"):
+        {"traffic": 379714816, "issue_active_pct": 47.9, "shared_pipe_pct": 17.4},
+}
 
 
 def parse():
@@ -631,6 +641,7 @@ def run_flashmap(args):
     counters = NCU_COUNTERS.get((args.workload, source_digest()), {})
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
             "frac": achieved / peak, "traffic": counters.get("traffic"),
+            "traffic_basis": counters.get("traffic_basis"),
             "kernel": "fr_map_kernel", "kernel_ms": 1e3 * kmean,
             "ops_per_launch": ops, "peak_basis": basis,
             "issue_active_pct": counters.get("issue_active_pct"),
