@@ -32,8 +32,8 @@ __host__ __device__ inline CtaLayout fr_cta_layout(int stages, int tile_bytes,
   c.tiles = 0;
   c.bars = stages * tile_bytes;
   c.slots = c.bars + 2 * stages * 8;
-  c.fb = c.slots + stages * 4;  // pool: count, next, kFbTasks tasks
-  c.arenas = fr_align(c.fb + (2 + kFbTasks) * 4, 128);
+  c.fb = c.slots + stages * 4;  // pool: count, next, count_big, next_big, kFbTasks tasks
+  c.arenas = fr_align(c.fb + (4 + kFbTasks) * 4, 128);
   c.bytes = c.arenas + nw * arena_bytes;
   return c;
 }
@@ -113,11 +113,11 @@ __device__ __noinline__ void feed(const FrMapArgs& args, Feeder& fd, int stage,
 // refill: this is the item's last round, so once every warp has gathered its
 // window the feeder reloads buffer `stage` (next barrier phase `parity`).
 template <bool DUMP>
-__device__ void map_voxel(const FrMapArgs& args, const FrJob& job,
-                          const FrItem& item, const uint32_t* tile, int t, bool has,
-                          Arena& A, char* smem_big, char* slab_big, int it, int nt,
-                          Feeder& fd, bool refill, int stage, unsigned parity,
-                          const FbPool& pool, unsigned char* arenas) {
+__device__ __forceinline__ void map_voxel(const FrMapArgs& args, const FrJob& job,
+                                          const FrItem& item, const uint32_t* tile, int t, bool has,
+                                          Arena& A, char* smem_big, char* slab_big, int it, int nt,
+                                          Feeder& fd, bool refill, int stage, unsigned parity,
+                                          const FbPool& pool, unsigned char* arenas) {
   const int lane = lane_id();
   Win w;
   int col = 0;
@@ -190,13 +190,15 @@ __device__ void map_voxel(const FrMapArgs& args, const FrJob& job,
     if (work) glcm_family(w, A, job, d_glcm, use_pool ? &pool : nullptr);
     if (use_pool) {
       consumer_bar(nt);  // the task list is complete
-      if (*(volatile int*)pool.count > 0) {
+      if (*(volatile int*)pool.count + *(volatile int*)pool.count_big > 0) {
         const int s = 2 * job.r + 1;
         fb_pool_work(pool, args, s * s * s, arenas, args.arena.bytes, args.arena.off_big, smem_big);
         consumer_bar(nt);  // every radius is in its owner's results
         if (threadIdx.x == 0) {
           *pool.count = 0;
           *pool.next = 0;
+          *pool.count_big = 0;
+          *pool.next_big = 0;
         }
       }
     }
@@ -251,8 +253,7 @@ __global__ void __launch_bounds__(32 * kMaxConsumerWarps, 1)
     for (int s = 0; s < S; ++s) mbar_init(&fd.full[s], 1);
     fence_mbar_init();
     int* fbc = (int*)(smem + cl.fb);
-    fbc[0] = 0;
-    fbc[1] = 0;
+    for (int q = 0; q < 4; ++q) fbc[q] = 0;
   }
   // zero this warp's arena (the count matrices must start at zero)
   {
@@ -282,7 +283,9 @@ __global__ void __launch_bounds__(32 * kMaxConsumerWarps, 1)
   FbPool pool;
   pool.count = (int*)(smem + cl.fb);
   pool.next = pool.count + 1;
-  pool.tasks = pool.count + 2;
+  pool.count_big = pool.count + 2;
+  pool.next_big = pool.count + 3;
+  pool.tasks = pool.count + 4;
   pool.scratch = args.fb ? args.fb + ((size_t)blockIdx.x * NW + warp) * args.fb_stride : nullptr;
   pool.warp = warp;
   int stage = 0;

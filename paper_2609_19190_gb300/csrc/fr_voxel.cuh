@@ -867,6 +867,114 @@ __device__ float pool_rho_regs(const float* __restrict__ src, int n) {
   return 0.5f * (lo + hi);
 }
 
+// Largest |eigenvalue| of two symmetric matrices of at most 16 rows at once,
+// one per half-warp: lanes 16 h .. 16 h + 15 take the n x n matrix at src
+// (dense, row stride n; n = 0: no matrix), lane i of the half holding row i.
+// The Householder steps of pool_rho_regs with every sum over the half (xor
+// butterflies of width 16); a column already reduced takes a zero reflector
+// instead of a branch, so both halves run the same instructions and every
+// shuffle sees the whole warp.  Then Sturm-count multisection over 16 shifts
+// per round, one per lane of the half, of [max_i |T e_i|, B] (B the smaller
+// of the Gershgorin and Frobenius bounds; |T e_i| <= rho), until the bracket
+// is at most max(1e-6, 2e-5 lo) wide.  A shift counts the eigenvalues of
+// either sign beyond it until the counts at the bracket's lower end show one
+// end of the spectrum alone beyond it; that end decides the radius, and
+// later rounds count it alone.  Every lane of a half returns its matrix's
+// value.
+static __device__ __forceinline__ float pool_rho_half16(const float* __restrict__ src, int n) {
+  constexpr int N = 16;
+  const int lane = lane_id();
+  const int r = lane & 15, half = lane >> 4;
+  float a[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) a[j] = (r < n && j < n) ? src[r * n + j] : 0.f;
+  float dk = 0.f, ek = 0.f;  // lane k of the half ends with d_k and e_k
+#pragma unroll
+  for (int k = 0; k + 2 < N; ++k) {
+    const float x = r > k ? a[k] : 0.f;
+    const float x1 = __shfl_sync(kFull, a[k], k + 1, 16);
+    float tail = r > k + 1 ? x * x : 0.f;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) tail += __shfl_xor_sync(kFull, tail, o);
+    if (r == k) dk = a[k];
+    const bool red = tail == 0.f;  // the same on every lane of the half
+    const float alpha = red ? x1 : -copysignf(sqrtf(tail + x1 * x1), x1);
+    const float inv = red ? 0.f : rsqrtf(2.f * (alpha * alpha - alpha * x1));
+    const float v = r > k ? (r == k + 1 ? x1 - alpha : x) * inv : 0.f;
+    float vb[N];
+    float p = 0.f;
+#pragma unroll
+    for (int j = k + 1; j < N; ++j) {
+      vb[j] = __shfl_sync(kFull, v, j, 16);
+      p = fmaf(a[j], vb[j], p);
+    }
+    float kp = v * p;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) kp += __shfl_xor_sync(kFull, kp, o);
+    const float w = p - kp * v;
+#pragma unroll
+    for (int j = k + 1; j < N; ++j) {
+      const float wj = __shfl_sync(kFull, w, j, 16);
+      a[j] -= 2.f * (v * wj + w * vb[j]);
+    }
+    if (r == k) ek = alpha;
+  }
+  if (r == N - 2) {
+    dk = a[N - 2];
+    ek = a[N - 1];
+  }
+  if (r == N - 1) dk = a[N - 1];
+  float d[N], e2[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    d[i] = __shfl_sync(kFull, dk, i, 16);
+    const float e = __shfl_sync(kFull, ek, i, 16);
+    e2[i] = e * e;
+  }
+  float gb = 0.f, fro = 0.f, cn = 0.f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float g = fabsf(d[i]), c = d[i] * d[i];
+    if (i > 0) {
+      g += sqrtf(e2[i - 1]);
+      c += e2[i - 1];
+    }
+    if (i < N - 1) {
+      g += sqrtf(e2[i]);
+      c += e2[i];
+    }
+    gb = fmaxf(gb, g);
+    cn = fmaxf(cn, c);
+    fro = fmaf(d[i], d[i], fmaf(2.f, e2[i], fro));
+  }
+  float lo = sqrtf(cn) * 0.9999f, hi = fminf(gb, sqrtf(fro)) * 1.0001f + 1e-20f;
+  int ends = 0;  // 0: both ends; 1: the top end decides; 2: the bottom end
+  for (int round = 0; round < 8; ++round) {
+    const bool done = hi - lo <= fmaxf(1e-6f, 2e-5f * lo);
+    if (__all_sync(kFull, done)) break;
+    const float step = (hi - lo) * (1.f / 17.f);
+    const float sig = lo + step * (float)(r + 1);
+    // eigenvalues above sig (below -sig: of -T above sig) at the end taken,
+    // and below -sig while both ends are counted
+    const int ca = N - sturm_count<N>(d, e2, ends == 2 ? -1.f : 1.f, sig);
+    const int cb = ends == 0 ? sturm_count<N>(d, e2, 1.f, -sig) : 0;
+    const unsigned msk = (__ballot_sync(kFull, ca + cb > 0) >> (16 * half)) & 0xFFFFu;
+    const int L = msk ? 31 - __clz(msk) : 0;
+    const int at = __shfl_sync(kFull, (ca > 0 ? 1 : 0) | (cb > 0 ? 2 : 0), L, 16);
+    if (!done) {
+      if (msk == 0u) {
+        hi = lo + step;
+      } else {
+        const float nlo = lo + step * (float)(L + 1);
+        const float nhi = (L == 15) ? hi : lo + step * (float)(L + 2);
+        lo = nlo;
+        hi = nhi;
+        if (ends == 0 && at != 3) ends = at;
+      }
+    }
+  }
+  return 0.5f * (lo + hi);
+}
 
 // Largest |eigenvalue| of a symmetric N x N matrix read from a packed upper
 // triangle in the kCapL x kCapL layout, by one thread with every value in
@@ -1159,12 +1267,24 @@ __device__ __forceinline__ float kl_term(float d) {
 // and writes the radius into the owner's results, so one voxel's many-level
 // directions no longer hold the whole CTA at the next barrier.
 struct FbPool {
-  int* count;        // tasks listed this round
-  int* next;         // next task to take
+  int* count;        // tasks of up to 16 rows listed this round (from the front)
+  int* next;         // next of them to take
+  int* count_big;    // tasks of more rows (from the back of the list)
+  int* next_big;
   int* tasks;        // owner warp << 16 | direction << 8 | size
   float* scratch;    // this warp's matrices, kNumDirs x kMCap^2
   int warp;
 };
+
+// Lists warp-owner direction d's m x m solve: up to 16 rows at the front of
+// the list (the pool solves two at a time), more at the back.
+__device__ __forceinline__ void pool_list(const FbPool* pool, int d, int m) {
+  const int task = (pool->warp << 16) | (d << 8) | m;
+  if (m <= 16)
+    pool->tasks[atomicAdd(pool->count, 1)] = task;
+  else
+    pool->tasks[kFbTasks - 1 - atomicAdd(pool->count_big, 1)] = task;
+}
 
 // After the 13 directions: the deferred MCC solves (one lane per direction),
 // the direction means, and ClusterShade's mean (in float pairs).
@@ -1568,8 +1688,7 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
           if (lane == 0) {
             mn[ds] = 0;
             mres[ds] = kNaNf;  // the pool writes the radius
-            const int slot_i = atomicAdd(pool->count, 1);
-            pool->tasks[slot_i] = (pool->warp << 16) | (ds << 8) | m;
+            pool_list(pool, ds, m);
           }
         } else {
           const float rho = spectral_radius(Sm, m, mc, vv, ww, dd, ee);
@@ -1683,19 +1802,38 @@ static __device__ void fb_pool_work(const FbPool& P, const FrMapArgs& args, int 
                                     char* my_big) {
   const int lane = lane_id();
   const BigLayout L = fr_big_layout(kMCap, kBinCap, W);
-  const int count = *(volatile int*)P.count;
+  const int count = *(volatile int*)P.count, count_big = *(volatile int*)P.count_big;
   (void)my_big;
+  const float* fb = args.fb + (size_t)blockIdx.x * args.consumer_warps * args.fb_stride;
+  // tasks have more than kCapL levels: two of 13..16 rows at once, one per
+  // half-warp, then the larger ones (17..kMCap rows) by the whole warp
   while (true) {
     int t = 0;
-    if (lane == 0) t = atomicAdd(P.next, 1);
+    if (lane == 0) t = atomicAdd(P.next, 2);
     t = __shfl_sync(kFull, t, 0);
     if (t >= count) break;
-    const int task = P.tasks[t];
+    const int task0 = P.tasks[t];
+    const int task1 = t + 1 < count ? P.tasks[t + 1] : -1;
+    const int task = (lane >> 4) ? task1 : task0;
+    const int n = task >= 0 ? (task & 0xFF) : 0;
+    const int owner = task >> 16, d = (task >> 8) & 0xFF;
+    const float* src = n > 0 ? fb + (size_t)owner * args.fb_stride + (size_t)d * kFbDir : fb;
+    const float rho = pool_rho_half16(src, n);
+    if ((lane & 15) == 0 && n > 0) {
+      float* mres = (float*)(arenas + (size_t)owner * arena_bytes + arena_off_big + L.mres);
+      mres[d] = rho;
+    }
+    __syncwarp();
+  }
+  while (true) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(P.next_big, 1);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= count_big) break;
+    const int task = P.tasks[kFbTasks - 1 - t];
     const int owner = task >> 16, d = (task >> 8) & 0xFF, n = task & 0xFF;
-    const float* src = args.fb + ((size_t)blockIdx.x * args.consumer_warps + owner) * args.fb_stride +
-                       (size_t)d * kFbDir;
-    // tasks have more than kCapL levels: 13..16 or 17..kMCap rows
-    const float rho = n <= 16 ? pool_rho_regs<16>(src, n) : pool_rho_regs<kMCap>(src, n);
+    const float* src = fb + (size_t)owner * args.fb_stride + (size_t)d * kFbDir;
+    const float rho = pool_rho_regs<kMCap>(src, n);
     if (lane == 0) {
       float* mres = (float*)(arenas + (size_t)owner * arena_bytes + arena_off_big + L.mres);
       mres[d] = rho;
@@ -1933,10 +2071,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
       if (!h) {
         mn[d] = slot ? present : 0;
         if (!slot) mres[d] = kNaNf;
-        if (many) {
-          const int ti = atomicAdd(pool->count, 1);
-          pool->tasks[ti] = (pool->warp << 16) | (d << 8) | m;
-        }
+        if (many) pool_list(pool, d, m);
       }
       __syncwarp(pm);
       unsigned a1 = 0, e2 = 0, maxc = 0;
