@@ -142,7 +142,10 @@ __device__ __forceinline__ void map_voxel(const FrMapArgs& args, const FrJob& jo
     const int cy = y - item.by;
     const int cz = z - item.bz;
     w.nv = gather_window(w, A, tile, job.box_x, job.box_y, cx, cy, cz);
-    warp_sort_x(A.kb, w.nv, (int*)(A.tmp + 32));
+    // the big region is free until the families: the counting sort's bins
+    const bool counting = w.nv > kCsortMinKeys && w.nv <= 32 * kRadixRounds;
+    if (!counting || !warp_csort(A.kb, w.nv, (uint32_t*)smem_big, args.arena.big_bytes >> 2))
+      warp_sort_x(A.kb, w.nv, (int*)(A.tmp + 32));
     if (DUMP) {
       const int ng = w.ng;
       int32_t* rec = args.dbg + (size_t)it * args.dbg_stride;

@@ -391,6 +391,86 @@ static __device__ void warp_sort_x(uint32_t* a, int n, int* hist) {
   }
 }
 
+// Ascending sort of the n window keys ((x + 32768) << 8 | level) in a[0..n)
+// by counting, for n <= 32 kRadixRounds and an intensity span
+// x_max - x_min + 1 of at most 2 nwords: one 16-bit count per intensity, two
+// to a word of `bins` (nwords words of shared scratch; the words the span
+// covers are zeroed first and left zero).  Counts by shared atomics, an
+// exclusive scan of the span (a run of words per lane, then across lanes),
+// and each key placed at the position its atomic increment returns.  Keys of equal x are equal
+// words, so the order in which equal keys land does not matter: the result
+// is the one sorted array.  Unlike the radix passes, no round waits for the
+// one before it.  Returns false, with a and bins untouched, when the span is
+// larger.
+constexpr int kCsortMinKeys = 0;  // windows of more keys are sorted by counting
+static __device__ bool warp_csort(uint32_t* a, int n, uint32_t* bins, int nwords) {
+  const int lane = lane_id();
+  const int rounds = (n + 31) >> 5;
+  uint32_t k[kRadixRounds];
+  unsigned lo = 0xffffffffu, hi = 0u;
+#pragma unroll
+  for (int r = 0; r < kRadixRounds; ++r) {
+    const int i = 32 * r + lane;
+    k[r] = 0u;
+    if (r < rounds && i < n) {
+      k[r] = a[i];
+      lo = min(lo, k[r] >> 8);
+      hi = max(hi, k[r] >> 8);
+    }
+  }
+  lo = __reduce_min_sync(kFull, lo);
+  hi = __reduce_max_sync(kFull, hi);
+  if (hi - lo >= 2u * (unsigned)nwords) return false;
+  const int nw = (int)((hi - lo) >> 1) + 1;  // words the span covers
+  for (int q = lane; q < nw; q += 32) bins[q] = 0u;
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < kRadixRounds; ++r) {
+    const int i = 32 * r + lane;
+    if (r < rounds && i < n) {
+      const unsigned v = (k[r] >> 8) - lo;
+      atomicAdd(&bins[v >> 1], 1u << ((v & 1u) << 4));
+    }
+  }
+  __syncwarp();
+  {  // exclusive scan: lane takes words [q0, q1)
+    const int per = (nw + 31) >> 5;
+    const int q0 = min(lane * per, nw), q1 = min(q0 + per, nw);
+    unsigned tot = 0u;
+    for (int q = q0; q < q1; ++q) {
+      const unsigned x = bins[q];
+      tot += (x & 0xffffu) + (x >> 16);
+    }
+    unsigned inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += y;
+    }
+    unsigned run = inc - tot;
+    for (int q = q0; q < q1; ++q) {
+      const unsigned x = bins[q];
+      const unsigned c0 = x & 0xffffu;
+      bins[q] = run | ((run + c0) << 16);
+      run += c0 + (x >> 16);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < kRadixRounds; ++r) {
+    const int i = 32 * r + lane;
+    if (r < rounds && i < n) {
+      const unsigned v = (k[r] >> 8) - lo, sh = (v & 1u) << 4;
+      const unsigned old = atomicAdd(&bins[v >> 1], 1u << sh);
+      a[(old >> sh) & 0xffffu] = k[r];
+    }
+  }
+  __syncwarp();
+  for (int q = lane; q < nw; q += 32) bins[q] = 0u;
+  __syncwarp();
+  return true;
+}
+
 // first index in a[lo..hi) with a[i] >= key (a sorted)
 __device__ __forceinline__ int lower_bound_u32(const uint32_t* a, int lo, int hi,
                                                uint32_t key) {
@@ -767,6 +847,33 @@ __device__ __forceinline__ int sturm_count(const float (&d)[N], const float (&e2
   return c;
 }
 
+// The same count from the leading principal minors of the first n rows
+// (rows beyond n are zero padding and left out):
+// p_k = det(sg T_k - t I) = (sg d_k - t) p_{k-1} - e2_{k-1} p_{k-2}, p_0 = 1,
+// and each sign change between p_{k-1} and p_k is one eigenvalue below t.
+// Two dependent operations per row instead of a reciprocal.  The caller
+// scales T (and t) to spectral radius <= 1, which keeps every minor of at
+// most 12 rows within float range; a minor that is exactly zero takes the
+// sign opposite to the one before it (a bias of 1e-37, below the rounding of
+// any other value), as the ratio form's guard does.
+template <int N>
+__device__ __forceinline__ int sturm_minors(const float (&d)[N], const float (&e2)[N], float sg,
+                                            float t, int n) {
+  float p0 = 1.f;
+  float p1 = fmaf(sg, d[0], -t) - 1e-37f;
+  int c = (int)(__float_as_uint(p1) >> 31);
+#pragma unroll
+  for (int i = 1; i < N; ++i) {
+    if (i < n) {
+      const float q = fmaf(fmaf(sg, d[i], -t), p1, -e2[i - 1] * p0) - copysignf(1e-37f, p1);
+      c += (int)((__float_as_uint(q) ^ __float_as_uint(p1)) >> 31);
+      p0 = p1;
+      p1 = q;
+    }
+  }
+  return c;
+}
+
 // Rounds of the paired MCC solve: both-ends bisection (one bit per round),
 // then trisection of the deciding end (log2 3 bits per round); about 22 bits
 // in all.
@@ -983,13 +1090,14 @@ static __device__ __forceinline__ float pool_rho_half16(const float* __restrict_
 // (A u = 0), so the radius is unchanged and one fixed N serves all smaller
 // matrices.  Householder tridiagonalisation (indices are compile-time
 // constants, so the loops unroll into independent FMAs), then Sturm
-// bisection of the two ends of the spectrum.  Two lanes solve each matrix
+// bisection of the two ends of the spectrum, counted from the leading minors
+// of the n x n block (n = the direction's present levels) of T / bound.  Two lanes solve each matrix
 // (h = 0, 1; pm = the pair's lane mask) and share every round's result: while
 // both ends are open, lane 0 bisects the top end and lane 1 the bottom one;
 // then the pair trisects the deciding end, one shift each.  Both lanes end
 // with the same bracket and return the same value.
 template <int N>
-__device__ __forceinline__ float rho_reg(const float* __restrict__ P, int h, unsigned pm) {
+__device__ __forceinline__ float rho_reg(const float* __restrict__ P, int h, unsigned pm, int n) {
   constexpr int NP = N * (N + 1) / 2;
   float a[NP];
 #pragma unroll
@@ -1052,6 +1160,13 @@ __device__ __forceinline__ float rho_reg(const float* __restrict__ P, int h, uns
     fro = fmaf(d[i], d[i], fmaf(2.f, e2[i], fro));
   }
   bnd = fminf(bnd, sqrtf(fro)) * 1.0001f + 1e-20f;
+  // the counts run on T / bnd (shifts t / bnd): spectral radius <= 1
+  const float sc = __fdividef(1.f, bnd);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    d[i] *= sc;
+    e2[i] = (e2[i] * sc) * sc;
+  }
   // A has the eigenvalue 0, so lambda_max >= 0 >= lambda_min and the radius
   // is max(lambda_max, -lambda_min).  Bracket both ends (lambda_max in
   // [max d_i, bnd], lambda_min in [-bnd, min d_i], by interlacing) until the
@@ -1063,7 +1178,8 @@ __device__ __forceinline__ float rho_reg(const float* __restrict__ P, int h, uns
     // lane 0: top bracket [hl, hh] of A; lane 1: top bracket [-lh, -ll] of -A
     const float lo = h ? -lh : hl, hi = h ? -ll : hh;
     const float t = 0.5f * (lo + hi);
-    const bool below = sturm_count<N>(d, e2, h ? -1.f : 1.f, t) == N;  // every eigenvalue < t
+    // every eigenvalue < t (the n x n block's; t > 0, so the padding's zeros too)
+    const bool below = sturm_minors<N>(d, e2, h ? -1.f : 1.f, t * sc, n) == n;
     const float nlo = below ? lo : t, nhi = below ? t : hi;
     const float olo = __shfl_xor_sync(pm, nlo, 16), ohi = __shfl_xor_sync(pm, nhi, 16);
     hl = h ? olo : nlo;
@@ -1080,12 +1196,12 @@ __device__ __forceinline__ float rho_reg(const float* __restrict__ P, int h, uns
     if (hi - lo <= fmaxf(1e-6f, 2e-5f * lo)) break;
     const float st = (hi - lo) * (1.f / 3.f);
     const float t1 = lo + st, t2 = lo + 2.f * st;
-    const int c = sturm_count<N>(d, e2, sg, h ? t2 : t1);
+    const int c = sturm_minors<N>(d, e2, sg, (h ? t2 : t1) * sc, n);
     const int co = __shfl_xor_sync(pm, c, 16);
     const int c1 = h ? co : c, c2 = h ? c : co;
-    if (c1 == N) {
+    if (c1 == n) {
       hi = t1;
-    } else if (c2 == N) {
+    } else if (c2 == n) {
       lo = t1;
       hi = t2;
     } else {
@@ -1307,9 +1423,9 @@ static __device__ void glcm_finish(const Arena& A, const FrJob& job) {
     if (nl >= 2) {
       const float* P = slots + dl * kSlot;
       const unsigned pm = (1u << dl) | (1u << (dl + 16));
-      const float r = nmax <= 4   ? rho_reg<4>(P, h, pm)
-                      : nmax <= 8 ? rho_reg<8>(P, h, pm)
-                                  : rho_reg<kCapL>(P, h, pm);
+      const float r = nmax <= 4   ? rho_reg<4>(P, h, pm, nl)
+                      : nmax <= 8 ? rho_reg<8>(P, h, pm, nl)
+                                  : rho_reg<kCapL>(P, h, pm, nl);
       if (!h) mres[dl] = r;
     }
     __syncwarp();
