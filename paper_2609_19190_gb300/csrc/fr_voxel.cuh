@@ -1971,23 +1971,29 @@ static __device__ void fb_pool_work(const FbPool& P, const FrMapArgs& args, int 
 // difference, by gray-level sum; ties by pair index), so that every class of
 // equal difference (sum) is contiguous and its count is final at its last
 // pair.
-// Layout of the path in the shared-memory big region, per window side:
-// side 3 and 5 take up to 16 levels with byte pair counts (a direction of a
-// side-5 window has at most 100 voxel pairs, so a count 2n <= 200), side 7 up
-// to 12 levels with 16-bit counts.  Rows have an odd number of words.
+// Layout of the path, per window side: up to 16 levels.  Sides 3 and 5 keep
+// everything in the shared-memory big region, with byte pair counts (a
+// direction of a side-5 window has at most 100 voxel pairs, so a count
+// 2n <= 200).  Side 7 needs 16-bit counts, and its count rows fill the big
+// region up to the MCC bookkeeping, so its level sets, marginals, pair orders
+// and class counts go to the window-key buffer (free once first order is
+// done; 512 keys, 2 KB, at side 7).  Count rows have an odd number of words
+// and the marginals are level-major, so the 13 lanes touch distinct banks.
 template <int S>
 struct DirLayout {
-  static constexpr int kLv = S <= 5 ? 16 : 12;
-  static constexpr int kPairs = kLv * (kLv + 1) / 2;  // 136 or 78
+  static constexpr int kLv = 16;
+  static constexpr int kPairs = kLv * (kLv + 1) / 2;  // 136
   using Cnt = typename std::conditional<(S <= 5), uint8_t, uint16_t>::type;
-  static constexpr int kRow = S <= 5 ? 140 : 78;      // counts per row
-  static constexpr int kMgRow = kLv + 1;              // marginals per row
-  static constexpr int kMg = S <= 5 ? 320 : 672;      // byte offsets
-  static constexpr int kW = S <= 5 ? 764 : 1012;
-  static constexpr int kOrd = kW + 13 * kRow * (int)sizeof(Cnt);
+  static constexpr bool kSplit = S == 7;              // side tables in the key buffer
+  static constexpr int kRow = S <= 5 ? 140 : 138;     // counts per row
+  static constexpr int kMg = S <= 5 ? 320 : 896;      // marginals [kLv][13]
+  static constexpr int kW = S <= 5 ? 764 : 0;         // count rows (big region)
+  static constexpr int kRowsEnd = kW + 13 * kRow * (int)sizeof(Cnt);
+  static constexpr int kOrd = S <= 5 ? kRowsEnd : kMg + kLv * 13 * 2;
   static constexpr int kOrdLen = (kPairs + 3) & ~3;
   static constexpr int kCnt = kOrd + 4 * kOrdLen;
-  static constexpr int kBytes = (kCnt + 192 + 15) / 16 * 16;
+  static constexpr int kSideEnd = kCnt + 192;
+  static constexpr int kBytes = ((kSplit ? kRowsEnd : kSideEnd) + 15) / 16 * 16;  // of big
 };
 
 template <int S>
@@ -1998,22 +2004,24 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
   using Cnt = typename Lay::Cnt;
   constexpr int kRounds = (Lay::kPairs + 31) / 32;
   static_assert(Lay::kLv * S * sizeof(W) <= Lay::kMg, "level sets");
-  static_assert(Lay::kMg + 13 * Lay::kMgRow * 2 <= Lay::kW, "marginals");
-  static_assert(13 * 27 * 4 <= Lay::kOrd - Lay::kW, "per-direction features over the rows");
+  static_assert(Lay::kMg + Lay::kLv * 13 * 2 <= (Lay::kSplit ? Lay::kOrd : Lay::kW), "marginals");
+  static_assert(13 * 27 * 4 <= Lay::kRowsEnd - Lay::kW, "per-direction features over the rows");
   static_assert(Lay::kBytes <= 3648, "below the MCC bookkeeping");
+  static_assert(!Lay::kSplit || Lay::kSideEnd <= 512 * 4, "side tables in the side-7 key buffer");
   static_assert(S > 5 || 2 * S * S * (S - 1) < 256, "byte counts");
   const int lane = lane_id();
   const int m = w.m;
   const int npairs = m * (m + 1) / 2;
   const bool want_mcc = (job.families & kFamMCC) != 0;
-  W* Lsm = (W*)A.big;                                   // [m][S] level sets
-  uint16_t* mg = (uint16_t*)(A.big + Lay::kMg);         // [13][kMgRow] marginals
+  char* const side = Lay::kSplit ? (char*)A.kb : A.big;  // region of the side tables
+  W* Lsm = (W*)side;                                    // [m][S] level sets
+  uint16_t* mg = (uint16_t*)(side + Lay::kMg);          // [kLv][13] marginals
   Cnt* wt = (Cnt*)(A.big + Lay::kW);                    // [13][kRow] pair counts
-  uint8_t* kord = (uint8_t*)(A.big + Lay::kOrd);        // pair at each difference position
+  uint8_t* kord = (uint8_t*)(side + Lay::kOrd);         // pair at each difference position
   uint8_t* sord = kord + Lay::kOrdLen;                  // pair at each sum position
   uint8_t* kpos = sord + Lay::kOrdLen;                  // difference | 0x80 at a class end
   uint8_t* spos = kpos + Lay::kOrdLen;                  // sum - 2 lev0 | 0x80 at a class end
-  uint8_t* cntk = (uint8_t*)(A.big + Lay::kCnt);        // [64] by difference
+  uint8_t* cntk = (uint8_t*)(side + Lay::kCnt);         // [64] by difference
   uint8_t* cnts = cntk + 64;                            // [128] by sum - 2 lev0
   float* fvd = (float*)(A.big + Lay::kW);               // [13][27], after the rows are read
   int* mn = (int*)(A.big + A.L.mn);
@@ -2151,7 +2159,6 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
       }
     } else {
       const float fT = (float)T, fT2 = fT * fT, invT = __fdividef(1.f, fT);
-      uint16_t* mrow = mg + d * Lay::kMgRow;
       Cnt* wrow = wt + d * Lay::kRow;
       // marginals c_a = |L_a & fwd(V)| + |L_a & bwd(V)| (both lanes)
       unsigned m1 = 0, m2 = 0, pmask = 0;
@@ -2163,7 +2170,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
           const W la = Lsm[a * S + z];
           c += (unsigned)(popc_w<W>(la & fV[z]) + popc_w<W>(la & bV[z]));
         }
-        if (!h) mrow[a] = (uint16_t)c;
+        if (!h) mg[a * kNumDirs + d] = (uint16_t)c;
         if (c) {
           const unsigned i = A.lev[a];
           m1 += i * c;
@@ -2199,7 +2206,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
         for (int z = 0; z < S; ++z) la[z] = Lsm[a * S + z];
         D.fwd(la, fa);
         D.bwd(la, ba);
-        const int ca = mrow[a];
+        const int ca = mg[a * kNumDirs + d];
         const unsigned i = A.lev[a];
         const int pa = __popc(pmask & ((1u << a) - 1u));
         int t = a * m - ((a * (a - 1)) >> 1);  // pair (a, a)
@@ -2216,7 +2223,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
             }
           }
           wrow[t] = (uint16_t)(2 * n);  // the pair's weight in both distributions
-          const int cb = mrow[b];
+          const int cb = mg[b * kNumDirs + d];
           if (!ca || !cb) continue;
           const unsigned mult = (a == b) ? 1u : 2u;
           const int pb = __popc(pmask & ((1u << b) - 1u));
