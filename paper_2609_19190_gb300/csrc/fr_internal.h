@@ -41,9 +41,9 @@ constexpr int kPadMaxSide = 7;
 constexpr int kPadCells = (kPadMaxSide + 2) * (kPadMaxSide + 2) * (kPadMaxSide + 2);
 constexpr int kMaxStages = 4;
 // CTA pool of many-level MCC solves: at most one per direction per warp;
-// each direction's S - u u^T is a dense m x m block (row stride m, so the
-// lines a solve touches are contiguous) in the warp's global scratch
-// (kFbDir floats per direction)
+// each direction's S - u u^T is the packed upper triangle of its m x m
+// matrix (m (m + 1) / 2 contiguous floats, each written once) in the warp's
+// global scratch (kFbDir floats per direction)
 constexpr int kFbTasks = kMaxConsumerWarps * kNumDirs;
 constexpr int kFbDir = kMCap * kMCap;
 

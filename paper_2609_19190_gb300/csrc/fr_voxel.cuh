@@ -897,9 +897,13 @@ __device__ float pool_rho_regs(const float* __restrict__ src, int n) {
   static_assert(N <= 32, "one row per lane");
   const int lane = lane_id();
   float a[N];
+  // packed index of (min(lane, j), max(lane, j)), stepped along the row
+  int idx = lane;
 #pragma unroll
-  for (int j = 0; j < N; ++j)
-    a[j] = (lane < n && j < n) ? src[lane * n + j] : 0.f;
+  for (int j = 0; j < N; ++j) {
+    a[j] = (lane < n && j < n) ? src[idx] : 0.f;
+    idx += j < lane ? max(n - j - 1, 0) : 1;  // >= 0 on lanes beyond the matrix too
+  }
   float dk = 0.f, ek = 0.f;  // lane k ends with d_k and e_k (the (k, k+1) entry)
 #pragma unroll
   for (int k = 0; k + 2 < N; ++k) {
@@ -955,11 +959,20 @@ __device__ float pool_rho_regs(const float* __restrict__ src, int n) {
     bnd = fmaxf(bnd, r);
   }
   float lo = 0.f, hi = bnd * 1.0001f + 1e-20f;
+  // the counts run on T / hi (shifts sig / hi): spectral radius <= 1
+  const float sc = __fdividef(1.f, hi);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    d[i] *= sc;
+    e2[i] = (e2[i] * sc) * sc;
+  }
   for (int round = 0; round < 6; ++round) {
     const float step = (hi - lo) * (1.f / 33.f);
     const float sig = lo + step * (float)(lane + 1);
-    // eigenvalues above sig plus eigenvalues below -sig
-    const int cnt = (N - sturm_count<N>(d, e2, 1.f, sig)) + sturm_count<N>(d, e2, 1.f, -sig);
+    // eigenvalues above sig plus eigenvalues below -sig (rows beyond n are
+    // zero padding: their eigenvalues 0 lie between)
+    const int cnt = (n - sturm_minors<N>(d, e2, 1.f, sig * sc, n)) +
+                    sturm_minors<N>(d, e2, 1.f, -sig * sc, n);
     const unsigned msk = __ballot_sync(kFull, cnt > 0);
     if (msk == 0u) {
       hi = lo + step;
@@ -976,25 +989,31 @@ __device__ float pool_rho_regs(const float* __restrict__ src, int n) {
 
 // Largest |eigenvalue| of two symmetric matrices of at most 16 rows at once,
 // one per half-warp: lanes 16 h .. 16 h + 15 take the n x n matrix at src
-// (dense, row stride n; n = 0: no matrix), lane i of the half holding row i.
-// The Householder steps of pool_rho_regs with every sum over the half (xor
-// butterflies of width 16); a column already reduced takes a zero reflector
-// instead of a branch, so both halves run the same instructions and every
-// shuffle sees the whole warp.  Then Sturm-count multisection over 16 shifts
-// per round, one per lane of the half, of [max_i |T e_i|, B] (B the smaller
-// of the Gershgorin and Frobenius bounds; |T e_i| <= rho), until the bracket
-// is at most max(1e-6, 2e-5 lo) wide.  A shift counts the eigenvalues of
-// either sign beyond it until the counts at the bracket's lower end show one
-// end of the spectrum alone beyond it; that end decides the radius, and
-// later rounds count it alone.  Every lane of a half returns its matrix's
-// value.
+// (packed upper triangle, pk(n, i, j); n = 0: no matrix), lane i of the half
+// holding row i.  Householder steps as in pool_rho_regs with every sum over
+// the half (xor butterflies of width 16); a column already reduced
+// takes a zero reflector instead of a branch, so both halves run the same
+// instructions and every shuffle sees the whole warp.  Then Sturm-count
+// multisection over 16 shifts per round, one per lane of the half, of
+// [max_i |T e_i|, B] (B the smaller of the Gershgorin and Frobenius bounds;
+// |T e_i| <= rho), until the bracket is at most max(1e-6, 2e-5 lo) wide.  A
+// shift counts the eigenvalues of either sign beyond it until the counts at
+// the bracket's lower end show one end of the spectrum alone beyond it; that
+// end decides the radius, and later rounds count it alone.  The counts are
+// the sign changes of the leading minors of the n x n block of T / B.  Every
+// lane of a half returns its matrix's value.
 static __device__ __forceinline__ float pool_rho_half16(const float* __restrict__ src, int n) {
   constexpr int N = 16;
   const int lane = lane_id();
   const int r = lane & 15, half = lane >> 4;
   float a[N];
+  // packed index of (min(r, j), max(r, j)), stepped along the row
+  int idx = r;
 #pragma unroll
-  for (int j = 0; j < N; ++j) a[j] = (r < n && j < n) ? src[r * n + j] : 0.f;
+  for (int j = 0; j < N; ++j) {
+    a[j] = (r < n && j < n) ? src[idx] : 0.f;
+    idx += j < r ? max(n - j - 1, 0) : 1;  // >= 0 on lanes beyond the matrix too
+  }
   float dk = 0.f, ek = 0.f;  // lane k of the half ends with d_k and e_k
 #pragma unroll
   for (int k = 0; k + 2 < N; ++k) {
@@ -1007,24 +1026,29 @@ static __device__ __forceinline__ float pool_rho_half16(const float* __restrict_
     const bool red = tail == 0.f;  // the same on every lane of the half
     const float alpha = red ? x1 : -copysignf(sqrtf(tail + x1 * x1), x1);
     const float inv = red ? 0.f : rsqrtf(2.f * (alpha * alpha - alpha * x1));
+    if (r == k) ek = alpha;
     const float v = r > k ? (r == k + 1 ? x1 - alpha : x) * inv : 0.f;
     float vb[N];
-    float p = 0.f;
+    float p0 = 0.f, p1 = 0.f;
 #pragma unroll
     for (int j = k + 1; j < N; ++j) {
       vb[j] = __shfl_sync(kFull, v, j, 16);
-      p = fmaf(a[j], vb[j], p);
+      if ((j - k) & 1)
+        p1 = fmaf(a[j], vb[j], p1);
+      else
+        p0 = fmaf(a[j], vb[j], p0);
     }
+    const float p = p0 + p1;
     float kp = v * p;
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) kp += __shfl_xor_sync(kFull, kp, o);
     const float w = p - kp * v;
+    const float v2 = -2.f * v, w2 = -2.f * w;
 #pragma unroll
     for (int j = k + 1; j < N; ++j) {
       const float wj = __shfl_sync(kFull, w, j, 16);
-      a[j] -= 2.f * (v * wj + w * vb[j]);
+      a[j] = fmaf(v2, wj, fmaf(w2, vb[j], a[j]));
     }
-    if (r == k) ek = alpha;
   }
   if (r == N - 2) {
     dk = a[N - 2];
@@ -1055,6 +1079,13 @@ static __device__ __forceinline__ float pool_rho_half16(const float* __restrict_
     fro = fmaf(d[i], d[i], fmaf(2.f, e2[i], fro));
   }
   float lo = sqrtf(cn) * 0.9999f, hi = fminf(gb, sqrtf(fro)) * 1.0001f + 1e-20f;
+  // the counts run on T / hi (shifts sig / hi): spectral radius <= 1
+  const float sc = __fdividef(1.f, hi);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    d[i] *= sc;
+    e2[i] = (e2[i] * sc) * sc;
+  }
   int ends = 0;  // 0: both ends; 1: the top end decides; 2: the bottom end
   for (int round = 0; round < 8; ++round) {
     const bool done = hi - lo <= fmaxf(1e-6f, 2e-5f * lo);
@@ -1062,9 +1093,10 @@ static __device__ __forceinline__ float pool_rho_half16(const float* __restrict_
     const float step = (hi - lo) * (1.f / 17.f);
     const float sig = lo + step * (float)(r + 1);
     // eigenvalues above sig (below -sig: of -T above sig) at the end taken,
-    // and below -sig while both ends are counted
-    const int ca = N - sturm_count<N>(d, e2, ends == 2 ? -1.f : 1.f, sig);
-    const int cb = ends == 0 ? sturm_count<N>(d, e2, 1.f, -sig) : 0;
+    // and below -sig while both ends are counted; rows beyond n are zero
+    // padding, whose eigenvalues 0 lie between
+    const int ca = n - sturm_minors<N>(d, e2, ends == 2 ? -1.f : 1.f, sig * sc, n);
+    const int cb = ends == 0 ? sturm_minors<N>(d, e2, 1.f, -sig * sc, n) : 0;
     const unsigned msk = (__ballot_sync(kFull, ca + cb > 0) >> (16 * half)) & 0xFFFFu;
     const int L = msk ? 31 - __clz(msk) : 0;
     const int at = __shfl_sync(kFull, (ca > 0 ? 1 : 0) | (cb > 0 ? 2 : 0), L, 16);
@@ -1631,12 +1663,11 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
     // warp-cooperative solve into the (zero) count region
     const bool fill_s = S > 0 && want_mcc && present > kCapL;
     const bool pooled = pool != nullptr && want_mcc && present > kCapL;
-    // pooled: dense m x m (row stride m, contiguous) in the warp's global
-    // scratch; else dense (stride mc) in place of the counts
+    // pooled: packed upper triangle over the m compact levels in the warp's
+    // global scratch (every pair written); else dense (stride mc) in place
+    // of the counts, which are zero where no present pair writes
     float* Sm = pooled ? pool->scratch + (size_t)ds * kFbDir : (float*)cnt;
-    const int ms = pooled ? m : mc;
-    if (fill_s && pooled)  // the pair lanes write only present pairs
-      for (int t = lane; t < mm2; t += 32) Sm[t] = 0.f;
+    const int ms = mc;
     float* P = slots + ds * kSlot;
     const float invT = __fdividef(1.f, fT);
     if (slot)
@@ -1677,7 +1708,11 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
         }
         const int ca = __shfl_sync(kFull, (int)cmask, a), cb = __shfl_sync(kFull, (int)cmask, b);
         const int pa = __shfl_sync(kFull, prank_l, a), pbk = __shfl_sync(kFull, prank_l, b);
-        if (!valid || !ca || !cb) continue;
+        if (!valid) continue;
+        if (!ca || !cb) {
+          if (fill_s && pooled) Sm[t] = 0.f;  // a level absent along the direction
+          continue;
+        }
         if (!n) {
           // an empty pair of present levels: its q = p_a p_b enters MI, and
           // S - u u^T is dense there (-u_a u_b)
@@ -1686,8 +1721,12 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
           const float v = (float)(-cc) * rsqrtf((float)ca * (float)cb) * invT;
           if (slot) P[pk(kCapL, pa, pbk)] = v;
           if (fill_s) {
-            Sm[a * ms + b] = v;
-            Sm[b * ms + a] = v;
+            if (pooled) {
+              Sm[t] = v;  // t = pk(m, a, b)
+            } else {
+              Sm[a * ms + b] = v;
+              Sm[b * ms + a] = v;
+            }
           }
           continue;
         }
@@ -1705,9 +1744,13 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
         const float v = (float)(ct - cc) * rsqrtf((float)ca * (float)cb) * invT;
         if (slot) P[pk(kCapL, pa, pbk)] = v;
         if (fill_s) {
+          if (pooled) {
+            Sm[t] = v;
+          } else {
             Sm[a * ms + b] = v;
             Sm[b * ms + a] = v;
           }
+        }
         atomicAdd(&sbin[i + j - 2 * w.lev0], 2 * n);
         atomicAdd(&dbin[j - i], 2 * n);
         if (dbg_glcm) {
@@ -1796,8 +1839,12 @@ static __device__ void glcm_family_impl(const Win& w, const Arena& A, const FrJo
             const long long num = (long long)C * T - (long long)ca * cb;
             v = __fdividef((float)num * rsqrtf((float)ca * (float)cb), fT);
           }
-          Sm[a * ms + b] = v;
-          Sm[b * ms + a] = v;
+          if (pooled) {
+            Sm[pk(m, a, b)] = v;
+          } else {
+            Sm[a * ms + b] = v;
+            Sm[b * ms + a] = v;
+          }
         }
         __syncwarp();
         if (pooled) {
@@ -2186,11 +2233,10 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
       const bool many = want_mcc && present > kCapL;
       const bool slot = want_mcc && present >= 2 && !many;
       float* P = slots + d * kSlot;
-      float* Sm = many ? pool->scratch + (size_t)d * kFbDir : nullptr;  // dense, row stride m
+      // packed upper triangle over the m compact levels (pair index t)
+      float* Sm = many ? pool->scratch + (size_t)d * kFbDir : nullptr;
       if (slot)
         for (int t = h; t < kSlot; t += 2) P[t] = 0.f;
-      if (many)
-        for (int t = h; t < m * m; t += 2) Sm[t] = 0.f;
       if (!h) {
         mn[d] = slot ? present : 0;
         if (!slot) mres[d] = kNaNf;
@@ -2224,7 +2270,10 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
           }
           wrow[t] = (uint16_t)(2 * n);  // the pair's weight in both distributions
           const int cb = mg[b * kNumDirs + d];
-          if (!ca || !cb) continue;
+          if (!ca || !cb) {
+            if (many) Sm[t] = 0.f;  // a level absent along d
+            continue;
+          }
           const unsigned mult = (a == b) ? 1u : 2u;
           const int pb = __popc(pmask & ((1u << b) - 1u));
           const long long cc = (long long)ca * cb;
@@ -2234,10 +2283,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
             mi0 += mult * (unsigned long long)cc;
             const float v = (float)(-cc) * rsqrtf((float)ca * (float)cb) * invT;
             if (slot) P[pk(kCapL, pa, pb)] = v;
-            if (many) {
-              Sm[a * m + b] = v;
-              Sm[b * m + a] = v;
-            }
+            if (many) Sm[t] = v;
             continue;
           }
           const unsigned j = A.lev[b];
@@ -2253,10 +2299,7 @@ __device__ void glcm_dir_lanes(const Win& w, const Arena& A, const FrJob& job,
           {
             const float v = (float)(ct - cc) * rsqrtf((float)ca * (float)cb) * invT;
             if (slot) P[pk(kCapL, pa, pb)] = v;
-            if (many) {
-              Sm[a * m + b] = v;
-              Sm[b * m + a] = v;
-            }
+            if (many) Sm[t] = v;
           }
           if (dbg_glcm) {
             int32_t* g = dbg_glcm + (size_t)d * w.ng * w.ng;
