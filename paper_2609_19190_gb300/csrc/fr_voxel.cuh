@@ -2966,6 +2966,7 @@ __device__ void glrlm_dir_regs(const Win& w, const Arena& A, int32_t* dbg_glrlm)
 #pragma unroll
     for (int z = 0; z < S; ++z) nr += (unsigned)popc_w<W>(st[z]);
     unsigned prev[kQ];
+    unsigned live = 0;  // bit q: level h + 2 q has runs longer than the current j
     unsigned glnu = 0, si = 0, si2 = 0, sj = 0, sj2 = 0, rlnu = 0;
     float f_inv_i2 = 0.f, f_j = 0.f, f_j_inv_i2 = 0.f, f_j_i2 = 0.f, f_jj_inv_i2 = 0.f,
           f_jj_i2 = 0.f, ent = 0.f;
@@ -2984,6 +2985,7 @@ __device__ void glrlm_dir_regs(const Win& w, const Arena& A, int32_t* dbg_glrlm)
         f_inv_i2 += (float)c * inv_i2[a];
       }
       prev[q] = c;
+      if (c) live |= 1u << q;
     }
 #pragma unroll
     for (int j = 1; j <= S; ++j) {
@@ -2999,7 +3001,9 @@ __device__ void glrlm_dir_regs(const Win& w, const Arena& A, int32_t* dbg_glrlm)
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
         const int a = h + 2 * q;
-        if (a < m) {
+        // a level without runs longer than j - 1 has none longer than j:
+        // its counts stay zero and it is left out (a < m where live)
+        if ((live >> q) & 1u) {
           unsigned c = 0;
           if (j < S) {
 #pragma unroll
@@ -3007,6 +3011,7 @@ __device__ void glrlm_dir_regs(const Win& w, const Arena& A, int32_t* dbg_glrlm)
           }
           const unsigned cnt = prev[q] - c;
           prev[q] = c;
+          if (!c) live &= ~(1u << q);
           if (cnt) {
             col += cnt;
             ui2 += cnt * i2t[a];
