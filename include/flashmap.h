@@ -127,7 +127,11 @@ typedef struct fr_map_params {
 } fr_map_params;
 
 /* Launch shape of the mapping kernel (the autotuner's knobs).  Zero fields
- * take built-in defaults. */
+ * take built-in defaults: bricks of 16 x 8 x 8 voxels where every kernel
+ * radius is at most 3 and the plan maps at least 100,000 VOI voxels (counted
+ * from host masks; a device mask counts its whole volume), else 8 x 4 x 4;
+ * 16 voxels per work item, 16 consumer warps, 1 stage, as many CTAs per SM
+ * as fit.  A server takes the large bricks up to radius 3. */
 typedef struct fr_tune {
   int32_t brick_x, brick_y, brick_z; /* voxels per brick; brick_x % 4 == 0      */
   int32_t voxels_per_item;           /* work-queue granularity (1..1024)       */

@@ -15,10 +15,10 @@ import os
 
 CANDIDATES = (
     dict(brick_x=8, brick_y=4, brick_z=4, voxels_per_item=16, consumer_warps=16, stages=1),
-    dict(brick_x=8, brick_y=4, brick_z=4, voxels_per_item=32, consumer_warps=16, stages=1),
-    dict(brick_x=8, brick_y=4, brick_z=4, voxels_per_item=16, consumer_warps=16, stages=2),
     dict(brick_x=8, brick_y=4, brick_z=4, voxels_per_item=16, consumer_warps=16, stages=3),
-    dict(brick_x=8, brick_y=4, brick_z=4, voxels_per_item=8, consumer_warps=16, stages=2),
+    dict(brick_x=8, brick_y=4, brick_z=4, voxels_per_item=16, consumer_warps=16, stages=2),
+    dict(brick_x=16, brick_y=8, brick_z=8, voxels_per_item=16, consumer_warps=16, stages=1),
+    dict(brick_x=16, brick_y=8, brick_z=8, voxels_per_item=32, consumer_warps=16, stages=1),
     dict(brick_x=16, brick_y=4, brick_z=4, voxels_per_item=16, consumer_warps=16, stages=1),
     dict(brick_x=8, brick_y=8, brick_z=4, voxels_per_item=16, consumer_warps=16, stages=1),
     dict(brick_x=8, brick_y=4, brick_z=4, voxels_per_item=16, consumer_warps=8, stages=1),
