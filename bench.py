@@ -44,15 +44,15 @@ ALU_LANES_PER_SM = 128  # fp32/int32 lanes per Blackwell SM
 # launch, issue-slot utilisation and shared-memory pipe utilisation (% of
 # peak), as summarised under profiles/.
 NCU_COUNTERS = {
-    # profiles/: 770 B of DRAM traffic per VOI voxel on the 492,804-voxel band
-    # of the same volume (32.9 MB read + 346.8 MB written), scaled by voxels
+    # profiles/: 479 B of DRAM traffic per VOI voxel on the 492,804-voxel band
+    # of the same volume (25.3 MB read + 210.8 MB written), scaled by voxels
     # to the 2,014,083-voxel launch; issue slots and shared-memory pipe from
     # the band's full capture
-    ("ct_large", "e4cb427f0f524ac6690cd6925da5c55f6c3c3850060fb8dd72c734ea8b19afb5"):
-        {"traffic": 1551889099, "traffic_basis": "band of 492,804 voxels, scaled by voxels",
-         "issue_active_pct": 47.9, "shared_pipe_pct": 17.4},
-    ("ct_large_slab16", "e4cb427f0f524ac6690cd6925da5c55f6c3c3850060fb8dd72c734ea8b19afb5"):
-        {"traffic": 379714816, "issue_active_pct": 47.9, "shared_pipe_pct": 17.4},
+    ("ct_large", "2e90018b3b1e1c7d5b2dfd580062e9a0e083cfdd792b12103b8785a8af037613"):
+        {"traffic": 964936717, "traffic_basis": "band of 492,804 voxels, scaled by voxels",
+         "issue_active_pct": 50.6, "shared_pipe_pct": 16.7},
+    ("ct_large_slab16", "2e90018b3b1e1c7d5b2dfd580062e9a0e083cfdd792b12103b8785a8af037613"):
+        {"traffic": 236099840, "issue_active_pct": 50.6, "shared_pipe_pct": 16.7},
 }
 
 
