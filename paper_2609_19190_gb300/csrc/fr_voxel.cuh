@@ -314,7 +314,8 @@ static __device__ void warp_sort(uint32_t* a, int n) {
 // add to hist), scans the 32 counts, and scatters round by round in order,
 // so every pass is stable.  hist: 32 ints of warp scratch.  Other n: the
 // bitonic network of warp_sort (in registers up to 128 keys, where it was
-// measured faster than these passes).
+// measured faster than these passes).  The mapping kernel sorts windows by
+// counting (warp_csort) and comes here only for spans too wide for its bins.
 constexpr int kRadixRounds = 16;
 static __device__ void warp_sort_x(uint32_t* a, int n, int* hist) {
   if (n <= 128 || n > 32 * kRadixRounds) return warp_sort(a, n);
@@ -880,18 +881,19 @@ __device__ __forceinline__ int sturm_minors(const float (&d)[N], const float (&e
 constexpr int kMccRounds1 = 22;
 constexpr int kMccRounds2 = 14;
 
-// Largest |eigenvalue| of the symmetric n x n matrix (n <= N <= 32, dense,
-// row stride n) at src, by one warp with the matrix in registers: lane i
-// holds row i (zero beyond n; zero rows and columns only add the eigenvalue
-// 0, which every deflated S - u u^T already has).  Householder
+// Largest |eigenvalue| of the symmetric n x n matrix (n <= N <= 32, packed
+// upper triangle, pk(n, i, j)) at src, by one warp with the matrix in
+// registers: lane i holds row i (zero beyond n; zero rows and columns only
+// add the eigenvalue 0, which every deflated S - u u^T already has).  Householder
 // tridiagonalisation with the step loop unrolled, so every row element is a
 // register: per step the column's tail norm is one warp sum, p = A v takes
 // v_j from lane j by shuffle, and the rank-2 update A -= 2 (v w^T + w v^T)
 // takes w_j the same way; rows above the step are never read again, so they
 // are left as they are.  Then Sturm-count multisection of [0, B] (B the
 // Gershgorin bound) over 32 shifts per round, one per lane, counting the
-// eigenvalues of either sign beyond the shift.  Every lane returns the same
-// value (warp sums by xor butterflies give every lane identical totals).
+// eigenvalues of either sign beyond the shift by the signs of the leading
+// minors of the n x n block of T / B.  Every lane returns the same value
+// (warp sums by xor butterflies give every lane identical totals).
 template <int N>
 __device__ float pool_rho_regs(const float* __restrict__ src, int n) {
   static_assert(N <= 32, "one row per lane");
