@@ -44,15 +44,15 @@ ALU_LANES_PER_SM = 128  # fp32/int32 lanes per Blackwell SM
 # launch, issue-slot utilisation and shared-memory pipe utilisation (% of
 # peak), as summarised under profiles/.
 NCU_COUNTERS = {
-    # profiles/: 479 B of DRAM traffic per VOI voxel on the 492,804-voxel band
-    # of the same volume (25.3 MB read + 210.8 MB written), scaled by voxels
+    # profiles/: 477 B of DRAM traffic per VOI voxel on the 492,804-voxel band
+    # of the same volume (24.8 MB read + 210.4 MB written), scaled by voxels
     # to the 2,014,083-voxel launch; issue slots and shared-memory pipe from
     # the band's full capture
-    ("ct_large", "2e90018b3b1e1c7d5b2dfd580062e9a0e083cfdd792b12103b8785a8af037613"):
-        {"traffic": 964936717, "traffic_basis": "band of 492,804 voxels, scaled by voxels",
-         "issue_active_pct": 50.6, "shared_pipe_pct": 16.7},
-    ("ct_large_slab16", "2e90018b3b1e1c7d5b2dfd580062e9a0e083cfdd792b12103b8785a8af037613"):
-        {"traffic": 236099840, "issue_active_pct": 50.6, "shared_pipe_pct": 16.7},
+    ("ct_large", "47d36ccb30ad34b976d0ebd50daadb834c44c01cd803c4f86cdde167701ab4d3"):
+        {"traffic": 961114699, "traffic_basis": "band of 492,804 voxels, scaled by voxels",
+         "issue_active_pct": 50.6, "shared_pipe_pct": 16.6},
+    ("ct_large_slab16", "47d36ccb30ad34b976d0ebd50daadb834c44c01cd803c4f86cdde167701ab4d3"):
+        {"traffic": 235164672, "issue_active_pct": 50.6, "shared_pipe_pct": 16.6},
 }
 
 
